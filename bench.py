@@ -1,0 +1,289 @@
+"""Throughput of the two-component pseudopotential D3Q19 step on one GB300.
+
+Workload (default): primary drainage in a synthetic sphere pack, 128^3 voxels,
+spheres of radius 8 by seeded relaxed random sequential addition to porosity
+0.38, 8 reservoir slices per end, non-wetting component injected at z = 0
+under a fixed capillary pressure, NEEM inlet/outlet, contact angle 45 deg,
+viscosity ratio 10, FP32.  A step is one full time step over every fluid
+voxel (density, wall density, force, collision, streaming, bounce-back, open
+planes).  Throughput counts fluid-node updates per second (MLUPS over fluid
+nodes; the all-voxel rate is in ``config``).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+For N > 1 run under torchrun: every rank runs an independent replica.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS (2-component D3Q19)"
+UNIT = "MLUPS"
+ALGO_BYTES_FP32 = 2 * 19 * 4 * 2 + 4  # pops read + written, plus the node's voxel index
+WORKLOAD = "drainage_pack_128"
+
+
+def workload_setup():
+    from paper_2207_01534_gb300 import inputs
+
+    solid, r1, r2 = inputs.drainage_pack_128()
+    tau = inputs.tau_for_viscosity_ratio(10.0)
+    xi = inputs.xi_of_theta(45.0)
+    # inlet density of component 1 for a capillary pressure Pc = P_in - P_out of
+    # 0.02 with the Eq. 12 pressure (inlet: rho2 ~ 0.03; outlet: rho2 = 1, rho1 ~ 0.03)
+    G, minor, pc = 3.5, 0.03, 0.02
+    p_out = (1.0 + minor) / 3.0 + G / 3.0 * minor
+    rho_in1 = (p_out + pc - minor / 3.0) / (1.0 / 3.0 + G / 3.0 * minor)
+    kw = dict(tau=tau, G=G, xi=xi, periodic=(1, 1, 0), open_axis=2, rho_in1=rho_in1, rho_out2=1.0)
+    cfg = {"workload": WORKLOAD, "grid": [128, 128, 128], "sphere_radius": 8, "porosity": 0.38, "reservoir": 8,
+           "M": 10, "theta_deg": 45, "G": G, "Pc": pc, "n_fluid": int((solid == 0).sum()),
+           "lups_basis": "fluid nodes", "l2": "inputs larger than L2 (populations alone 146 MB)"}
+    return solid, r1, r2, kw, cfg
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in self.rows if len(r) >= 9 for k in range(4) if r[5 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(sm)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2207_01534_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
+    None when there is none for the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    e = d.get(WORKLOAD, {}).get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
+
+
+def oracle_rate(solid, r1, r2, kw, steps, budget_s=30.0):
+    """The FP64 oracle on the host cores: MLUPS over fluid nodes."""
+    import oracle
+
+    o = oracle.Oracle(solid, **kw)
+    o.init_densities(r1, r2)
+    o.step(1)  # first touch
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps and (time.perf_counter() - t0) < budget_s:
+        o.step(1)
+        done += 1
+    dt = time.perf_counter() - t0
+    nf = int((solid == 0).sum())
+    return nf * done / dt / 1e6, done, dt
+
+
+def run_reference(args, rank, world):
+    solid, r1, r2, kw, cfg = workload_setup()
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    nf = int((solid == 0).sum())
+    import oracle
+
+    o = oracle.Oracle(solid, **kw)
+    o.init_densities(r1, r2)
+    o.step(max(args.warmup, 0))
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    dt = time.perf_counter() - t0
+    v = nf * args.steps / dt / 1e6
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg, "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": "%d full steps of the %s workload" % (args.steps, WORKLOAD)},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    from paper_2207_01534_gb300 import lbm
+
+    lbm.load()
+    solid, r1, r2, kw, cfg = workload_setup()
+    nf = cfg["n_fluid"]
+    nvox = solid.size
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        lat = lbm.Lattice(solid, kernel=args.kernel, stream=stream.cuda_stream, **kw)
+        lat.init_densities(r1, r2)
+        lat.step(args.warmup)
+        lat.synchronize()
+
+        # device-timed region: K steps on the context stream, inputs resident
+        clocks = ClockSampler(local)
+        l0 = lat.info()["launches"]
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lat.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        launches = lat.info()["launches"] - l0
+        ms = ev0.elapsed_time(ev1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        sat = lat.saturation()
+        assert np.isfinite(sat).all(), sat
+
+        # per-kernel device time of the same steps (events around each launch)
+        kms = lat.step_timed(args.steps) / args.steps
+        lat.synchronize()
+    names = ("dens", "wall", "fused", "plane", "pipeline")
+    dominant = names[int(np.argmax(kms))]
+    value = nf * args.steps * world / (ms / 1e3) / 1e6
+    peak, peak_kind = peaks()
+    fused_ms = float(kms[2]) if kms[2] > 0 else float(kms.max())
+    achieved = ALGO_BYTES_FP32 * nf / (fused_ms / 1e3) / 1e9
+    step_bytes_rate = ALGO_BYTES_FP32 * nf / (ms / args.steps / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": measured_traffic("k_fused"), "kernel": "k_fused", "peak_kind": peak_kind,
+            "algorithmic_bytes_per_node": ALGO_BYTES_FP32, "kernel_ms": {names[k]: float(kms[k]) for k in range(5)},
+            "step_frac": step_bytes_rate / peak}
+    del lat
+    torch.cuda.synchronize()
+
+    # end to end through the public API with host buffers: create (geometry
+    # upload), initial densities upload, K steps, fields and saturation read back
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat2 = lbm.Lattice(solid, kernel=args.kernel, **kw)
+    lat2.init_densities(r1, r2)
+    lat2.step(args.steps)
+    fields = lat2.fields(("rho1", "rho2"))
+    s2 = lat2.saturation()
+    dt = time.perf_counter() - t0
+    del lat2, fields
+    h2d = solid.nbytes + r1.nbytes + r2.nbytes
+    d2h = 2 * nvox * 8 + 4 * 8
+    e2e = {"value": nf * args.steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+           "d2h_bytes_per_step": d2h / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, done, cdt = oracle_rate(solid, r1, r2, kw, steps=args.cpu_steps)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d full steps of the %s workload (%.1f s)" % (done, WORKLOAD, cdt)}
+    cfg = dict(cfg)
+    cfg.update({"parallelism": "replicas" if world > 1 else "single", "kernel_schedule": args.kernel,
+                "voxel_mlups": nvox * args.steps * world / (ms / 1e3) / 1e6})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "saturation": {"S_w": sat[0], "S_nw_smooth": sat[1]}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
+    ap.add_argument("--kernel", default="auto", choices=("auto", "split", "fused"))
+    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    assert args.warmup >= 0 and args.steps > 0
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,202 @@
+/*
+ * lbm.h -- C ABI of liblbm, a GB300 (sm_103a) implementation of the time step
+ * of the improved two-component pseudopotential lattice Boltzmann method of
+ * Sedahmed et al., Phys. Fluids (2022), arXiv 2207.01534, on a D3Q19 lattice
+ * over the fluid voxels of a porous geometry.
+ *
+ * Conventions for every call:
+ *   - Errors are returned as lbm_status codes; nothing throws across the ABI.
+ *     After a failure, lbm_last_error(ctx) returns a human-readable reason
+ *     (for lbm_create, lbm_last_error(NULL) holds the reason).
+ *   - Dense host arrays are indexed v = x + nx*(y + ny*z) (x fastest), and all
+ *     host arrays are owned by the caller; the library copies what it needs and
+ *     keeps no host pointer after a call returns.
+ *   - Device work is issued on the context's CUDA stream (default: the legacy
+ *     default stream; see lbm_set_stream).  lbm_step only enqueues work.
+ *     Calls that return host data (read_fields, saturation, get_populations,
+ *     synchronize) synchronise that stream.
+ *   - A context belongs to the device that was current at lbm_create; call it
+ *     with that device current.  Contexts are not thread-safe.
+ *
+ * Component 1 is the droplet / injected fluid ("oil"), component 2 the
+ * surrounding / initially saturating fluid ("water") (Section 2, Section 4.1).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_ERR_ARG = -1,       /* invalid argument or geometry */
+    LBM_ERR_ALLOC = -2,     /* device or host allocation failed */
+    LBM_ERR_CUDA = -3,      /* a CUDA call failed (message in lbm_last_error) */
+    LBM_ERR_NONFINITE = -4, /* the periodic check found a NaN/Inf density (sticky) */
+    LBM_ERR_DRIFT = -5,     /* mass drift above the limit on a closed domain (sticky) */
+    LBM_ERR_TIMEOUT = -6,   /* a bounded device wait gave up (sticky) */
+    LBM_ERR_UNSUPPORTED = -7
+} lbm_status;
+
+/* Population storage precision.  Arithmetic is FP32 for the 32- and 16-bit
+ * forms and FP64 for LBM_STORE_FP64. */
+enum {
+    LBM_STORE_FP32 = 0,
+    LBM_STORE_FP64 = 1,
+    LBM_STORE_FP16DEV = 2, /* moving populations as FP16 deviations from w_i*rho_ref */
+    LBM_STORE_BF16DEV = 3  /* same with BF16 */
+};
+
+/* Kernel schedule for the FP32/FP16/BF16 step. */
+enum {
+    LBM_KERNEL_AUTO = 0,
+    LBM_KERNEL_SPLIT = 1, /* density, wall and fused collide-stream passes */
+    LBM_KERNEL_FUSED = 2  /* single persistent pass per step (see lbm_step) */
+};
+
+enum { LBM_BC_NEEM = 0 };
+
+/* Field selection bits for lbm_read_fields. */
+enum {
+    LBM_FIELD_RHO1 = 1u,
+    LBM_FIELD_RHO2 = 2u,
+    LBM_FIELD_UX = 4u,
+    LBM_FIELD_UY = 8u,
+    LBM_FIELD_UZ = 16u,
+    LBM_FIELD_P = 32u
+};
+
+/* Geometry of one domain.  solid: nx*ny*nz bytes, nonzero = solid (phi = 1 of
+ * Eq. 14).  periodic[a] != 0 makes axis a periodic.  open_axis = -1: no open
+ * boundary; open_axis = 2: the z = 0 plane is the inlet and z = nz-1 the outlet
+ * (Section 2 inlet/outlet rules; only the z axis is supported).  A fluid voxel
+ * may touch a non-periodic face only across the open planes: closed faces must
+ * be solid voxels.  sample_lo <= z < sample_hi selects the slab that
+ * lbm_saturation counts (hi <= lo: the whole domain).  xi_field (optional,
+ * nx*ny*nz floats) gives the wettability parameter xi per solid voxel (Eq. 15
+ * chi); NULL uses params.xi everywhere. */
+typedef struct {
+    int32_t nx, ny, nz;
+    const uint8_t *solid;
+    int32_t periodic[3];
+    int32_t open_axis;
+    int32_t sample_lo, sample_hi;
+    const float *xi_field;
+} lbm_geometry;
+
+/* Model parameters (Section 2).  tau: relaxation times tau^(1), tau^(2)
+ * (Eq. 7, read as nu = c_s^2 (tau - 1/2)).  G: cohesion strength G_coh (Eq.
+ * 11; the paper uses 3.5).  xi: wettability, chi^(1) = 1 + xi, chi^(2) = 1 - xi
+ * (Eq. 15).  rho_in1 / rho_out2: prescribed component densities at the inlet
+ * and outlet planes (non-equilibrium extrapolation).  body_force: acceleration
+ * g, F^b = rho^sigma g (Eq. 10).  velocity_shift: 1 adds F^sigma/2 to the
+ * component momenta in Eq. 8 (the explicit-forcing reading, default); 0 uses
+ * the printed Eq. 4 momenta.  storage: LBM_STORE_*.  rho_ref: per-component
+ * reference density for the 16-bit deviation storage.  reduce_every: n > 0
+ * runs the FP64 finiteness / mass check every n steps inside lbm_step.
+ * kernel: LBM_KERNEL_*. */
+typedef struct {
+    double tau[2];
+    double G;
+    double xi;
+    double rho_in1, rho_out2;
+    double body_force[3];
+    int32_t bc;
+    int32_t storage;
+    int32_t velocity_shift;
+    int32_t reduce_every;
+    double rho_ref[2];
+    int32_t kernel;
+    double drift_limit; /* relative mass drift that raises LBM_ERR_DRIFT (closed domains) */
+} lbm_params;
+
+/* Sizes and counters of a context. */
+typedef struct {
+    int64_t n_fluid;        /* fluid nodes N_f */
+    int64_t n_wall;         /* solid voxels with at least one fluid neighbour */
+    int64_t n_voxels;       /* nx*ny*nz */
+    int64_t step;           /* time steps taken since the last initialisation */
+    int64_t device_bytes;   /* device memory held by the context */
+    int64_t launches;       /* kernels launched by this context so far */
+    int32_t storage;
+    int32_t kernel;         /* schedule actually used */
+} lbm_info;
+
+/* Fill *p with the defaults: tau = (1, 1), G = 3.5, xi = 0, rho_in1 = rho_out2
+ * = 1, no body force, NEEM, FP32, velocity_shift = 1, reduce_every = 0,
+ * rho_ref = (0, 0), kernel AUTO, drift_limit = 1e-6. */
+lbm_status lbm_default_params(lbm_params *p);
+
+/* Create a context: validates the geometry, builds the compact fluid index,
+ * neighbour data and wall list on the host, allocates device memory (through
+ * the allocator set by lbm_set_allocator, else cudaMalloc) and uploads it.
+ * Populations start at zero: call lbm_init_densities or lbm_set_populations. */
+lbm_status lbm_create(const lbm_geometry *geom, const lbm_params *params, lbm_ctx **out);
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Device allocator used by later lbm_create calls in this process (for
+ * example a framework's caching allocator).  alloc(bytes, user) returns a
+ * device pointer or NULL; free(ptr, user) releases it.  Pass NULL, NULL to
+ * restore cudaMalloc / cudaFree. */
+lbm_status lbm_set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *), void *user);
+
+/* Rest-equilibrium initial state f_i = w_i rho^sigma (Eq. 2 with u = 0) from
+ * dense host densities (doubles, nx*ny*nz each; solid voxels ignored).  Resets
+ * the step counter and captures the frozen open-boundary populations (Section
+ * 2 open boundary rule 2: missing populations keep their initial values). */
+lbm_status lbm_init_densities(lbm_ctx *ctx, const double *rho1, const double *rho2);
+
+/* Set / get the post-stream populations f_i^sigma of every fluid voxel.
+ * Host layout [sigma][i][v], 2*19*nx*ny*nz doubles, D3Q19 order of Section 2;
+ * solid entries are ignored on set and written as 0 on get.  set resets the
+ * step counter and the frozen boundary populations like lbm_init_densities. */
+lbm_status lbm_set_populations(lbm_ctx *ctx, const double *f);
+lbm_status lbm_get_populations(lbm_ctx *ctx, double *f);
+
+/* Enqueue n time steps (Eqs. 1-15 with the inlet/outlet rules of Section 2).
+ * Returns the sticky status observed so far (a failed periodic check from an
+ * earlier step, a CUDA launch error), without synchronising. */
+lbm_status lbm_step(lbm_ctx *ctx, int64_t n);
+
+/* Same as lbm_step, and also accumulates the device time of each kernel of
+ * the split schedule into kernel_ms[0..nk) (density, wall, fused, plane,
+ * pipeline), measured with CUDA events on the context stream. */
+lbm_status lbm_step_timed(lbm_ctx *ctx, int64_t n, double *kernel_ms, int32_t nk);
+
+/* Fields of the current state into dense host arrays of n_per_field doubles
+ * (>= nx*ny*nz) each, in bit order RHO1, RHO2, UX, UY, UZ, P, packed
+ * consecutively for the bits set in mask.  u = u^eq (Eq. 8, Section 2), P by
+ * Eq. 12 over ordered pairs: c_s^2 (rho1 + rho2) + c_s^2 G rho1 rho2.  Solid
+ * voxels read 0.  Synchronises. */
+lbm_status lbm_read_fields(lbm_ctx *ctx, uint32_t mask, double *out, size_t n_per_field);
+
+/* FP64 reductions of the current state (Section 4.1): out[0] = S_w, fraction
+ * of sample fluid nodes with rho2 > rho1; out[1] = smooth non-wetting
+ * saturation, mean of rho1 / (rho1 + rho2) over the sample; out[2], out[3] =
+ * mass of components 1 and 2 over all fluid nodes.  Synchronises. */
+lbm_status lbm_saturation(lbm_ctx *ctx, double out[4]);
+
+/* Change the prescribed inlet density of component 1 (capillary-pressure
+ * ramp of Section 4.1); takes effect from the next lbm_step. */
+lbm_status lbm_set_inlet(lbm_ctx *ctx, double rho_in1);
+
+/* Use this CUDA stream (a cudaStream_t) for all later device work. */
+lbm_status lbm_set_stream(lbm_ctx *ctx, void *cuda_stream);
+
+/* Wait for all enqueued work; returns the sticky device status. */
+lbm_status lbm_synchronize(lbm_ctx *ctx);
+
+lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *info);
+const char *lbm_last_error(const lbm_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

@@ -1,0 +1,675 @@
+// lbm_capi.cu -- host side of liblbm: geometry preprocessing (compact fluid
+// index, neighbour flags, wall list, open planes), device memory, the C ABI
+// declared in include/lbm.h, and the schedule of kernels per time step.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbm.h"
+#include "lbm_internal.h"
+#include "lbm_kernels.cuh"
+
+using namespace lbm;
+
+namespace {
+
+std::string g_create_err;
+void *(*g_alloc)(size_t, void *) = nullptr;
+void (*g_free)(void *, void *) = nullptr;
+void *g_alloc_user = nullptr;
+
+constexpr int kNumTimed = 5;  // dens, wall, fused, plane, pipeline
+
+}  // namespace
+
+struct lbm_ctx {
+    int device = 0;
+    cudaStream_t stream = 0;
+    int nx = 0, ny = 0, nz = 0;
+    int64_t nv = 0;
+    int periodic[3] = {0, 0, 0};
+    int open_axis = -1;
+    lbm_params p{};
+    int storage = LBM_STORE_FP32;
+    int kernel = LBM_KERNEL_SPLIT;
+    DevState s{};
+    void *(*alloc_fn)(size_t, void *) = nullptr;
+    void (*free_fn)(void *, void *) = nullptr;
+    void *alloc_user = nullptr;
+    std::vector<void *> allocs;
+    int64_t step = 0, launches = 0, bytes = 0;
+    lbm_status sticky = LBM_OK;
+    std::string err;
+    double *d_partials = nullptr;
+    double *d_red = nullptr;
+    double *d_frozen = nullptr;
+    int *h_flag = nullptr;  // pinned, device-mapped status word
+    int *d_flag = nullptr;
+    double mass0[2] = {0, 0};
+    cudaEvent_t ev[kNumTimed + 1];
+    bool have_ev = false;
+};
+
+namespace lbm {
+
+__global__ void __launch_bounds__(kReduceThreads) k_reduce_final(const double *partials, int nblocks, double *out)
+{
+    __shared__ double sm[kReduceThreads / 32];
+    for (int k = 0; k < 6; ++k) {
+        double v = 0.0;
+        for (int b = threadIdx.x; b < nblocks; b += blockDim.x) v += partials[(long long)b * kReduceSlots + k];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            double w = threadIdx.x < kReduceThreads / 32 ? sm[threadIdx.x] : 0.0;
+            for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+            if (threadIdx.x == 0) out[k] = w;
+        }
+        __syncthreads();
+    }
+}
+
+// Sets status bits from a finished reduction: 1 = non-finite density,
+// 2 = relative mass drift above the limit (closed domains only).
+__global__ void k_check(const double *red, double m01, double m02, double limit, int closed, int *flag)
+{
+    int bits = 0;
+    if (red[5] > 0.0) bits |= 1;
+    if (closed) {
+        if (fabs(red[0] - m01) > limit * fabs(m01) || fabs(red[1] - m02) > limit * fabs(m02)) bits |= 2;
+    }
+    if (bits) atomicOr(flag, bits);
+}
+
+}  // namespace lbm
+
+namespace {
+
+lbm_status fail(lbm_ctx *c, lbm_status st, const std::string &msg)
+{
+    if (c)
+        c->err = msg;
+    else
+        g_create_err = msg;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *where)
+{
+    return fail(c, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void *dalloc(lbm_ctx *c, size_t bytes)
+{
+    if (bytes == 0) bytes = 256;
+    void *ptr = nullptr;
+    if (c->alloc_fn) {
+        ptr = c->alloc_fn(bytes, c->alloc_user);
+    } else if (cudaMalloc(&ptr, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        ptr = nullptr;
+    }
+    if (ptr) {
+        c->allocs.push_back(ptr);
+        c->bytes += (int64_t)bytes;
+    }
+    return ptr;
+}
+
+void dfree(lbm_ctx *c, void *ptr)
+{
+    if (!ptr) return;
+    for (size_t k = 0; k < c->allocs.size(); ++k)
+        if (c->allocs[k] == ptr) {
+            c->allocs.erase(c->allocs.begin() + (long)k);
+            break;
+        }
+    if (c->free_fn)
+        c->free_fn(ptr, c->alloc_user);
+    else
+        cudaFree(ptr);
+}
+
+// Run fn with the storage type of the context as a template tag.
+template <class Fn>
+void dispatch(const lbm_ctx *c, Fn &&fn)
+{
+    if (c->storage == LBM_STORE_FP64)
+        fn(double{});
+    else
+        fn(float{});
+}
+
+constexpr int kEx[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
+constexpr int kEy[19] = {0, 0, 0, 1, -1, 0, 0, 1, 1, -1, -1, 0, 0, 0, 0, 1, -1, 1, -1};
+constexpr int kEz[19] = {0, 0, 0, 0, 0, 1, -1, 0, 0, 0, 0, 1, 1, -1, -1, 1, 1, -1, -1};
+
+double weight(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+lbm_status check_launch(lbm_ctx *c, const char *where)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        c->sticky = LBM_ERR_CUDA;
+        return cuda_fail(c, e, where);
+    }
+    return LBM_OK;
+}
+
+lbm_status device_status(lbm_ctx *c)
+{
+    if (c->sticky != LBM_OK) return c->sticky;
+    const int f = c->h_flag ? *(volatile int *)c->h_flag : 0;
+    if (f & 1) return fail(c, LBM_ERR_NONFINITE, "non-finite density found by the periodic check");
+    if (f & 2) return fail(c, LBM_ERR_DRIFT, "mass drift above drift_limit");
+    if (f & 4) return fail(c, LBM_ERR_TIMEOUT, "a bounded device wait gave up");
+    return LBM_OK;
+}
+
+void run_reduce(lbm_ctx *c)
+{
+    dispatch(c, [&](auto tag) {
+        using TS = decltype(tag);
+        Ops<TS>::dens(c->s, (int)(c->step & 1), c->stream);
+        Ops<TS>::reduce(c->s, c->d_partials, kReduceBlocks, c->d_red, c->stream);
+    });
+    c->launches += 3;
+}
+
+lbm_status capture_initial_mass(lbm_ctx *c)
+{
+    run_reduce(c);
+    double red[kReduceSlots];
+    cudaError_t e = cudaMemcpyAsync(red, c->d_red, sizeof(red), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "initial mass");
+    c->mass0[0] = red[0];
+    c->mass0[1] = red[1];
+    if (c->h_flag) *c->h_flag = 0;
+    return LBM_OK;
+}
+
+// One time step of the split schedule.  ev != nullptr records events around
+// the kernels for lbm_step_timed.
+void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
+{
+    const int par = (int)(c->step & 1);
+    cudaStream_t st = c->stream;
+    dispatch(c, [&](auto tag) {
+        using TS = decltype(tag);
+        if (ev) cudaEventRecord(ev[0], st);
+        Ops<TS>::dens(c->s, par, st);
+        if (ev) cudaEventRecord(ev[1], st);
+        Ops<TS>::wall(c->s, st);
+        if (ev) cudaEventRecord(ev[2], st);
+        Ops<TS>::fused(c->s, par, st);
+        if (ev) cudaEventRecord(ev[3], st);
+        Ops<TS>::plane(c->s, 1 - par, st);
+        if (ev) cudaEventRecord(ev[4], st);
+    });
+    c->launches += 2 + (c->s.n_wall > 0 ? 1 : 0) + (c->s.open_z ? 1 : 0);
+    c->step++;
+    if (c->p.reduce_every > 0 && c->step % c->p.reduce_every == 0) {
+        run_reduce(c);
+        k_check<<<1, 1, 0, st>>>(c->d_red, c->mass0[0], c->mass0[1], c->p.drift_limit, c->s.open_z ? 0 : 1,
+                                 c->d_flag);
+        c->launches += 1;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_default_params(lbm_params *p)
+{
+    if (!p) return LBM_ERR_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->tau[0] = p->tau[1] = 1.0;
+    p->G = 3.5;
+    p->xi = 0.0;
+    p->rho_in1 = p->rho_out2 = 1.0;
+    p->bc = LBM_BC_NEEM;
+    p->storage = LBM_STORE_FP32;
+    p->velocity_shift = 1;
+    p->reduce_every = 0;
+    p->kernel = LBM_KERNEL_AUTO;
+    p->drift_limit = 1e-6;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_allocator(void *(*alloc)(size_t, void *), void (*free_fn)(void *, void *), void *user)
+{
+    if ((alloc == nullptr) != (free_fn == nullptr)) return LBM_ERR_ARG;
+    g_alloc = alloc;
+    g_free = free_fn;
+    g_alloc_user = user;
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!g || !p || !g->solid) return fail(nullptr, LBM_ERR_ARG, "geometry, params and solid must be non-NULL");
+    const int nx = g->nx, ny = g->ny, nz = g->nz;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_ERR_ARG, "dimensions must be positive");
+    const int64_t nv = (int64_t)nx * ny * nz;
+    if (nv >= (int64_t)1 << 31) return fail(nullptr, LBM_ERR_ARG, "at most 2^31 - 1 voxels per domain");
+    if (g->open_axis != -1 && g->open_axis != 2)
+        return fail(nullptr, LBM_ERR_UNSUPPORTED, "open_axis must be -1 or 2 (z)");
+    const bool open_z = g->open_axis == 2;
+    if (open_z && (g->periodic[2] || nz < 3))
+        return fail(nullptr, LBM_ERR_ARG, "the open axis must be non-periodic and at least 3 voxels long");
+    if (p->storage != LBM_STORE_FP32 && p->storage != LBM_STORE_FP64)
+        return fail(nullptr, LBM_ERR_UNSUPPORTED, "storage type not supported by this build");
+    if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau must exceed 1/2");
+    if (p->bc != LBM_BC_NEEM) return fail(nullptr, LBM_ERR_UNSUPPORTED, "only the NEEM boundary is supported");
+    if (p->reduce_every < 0) return fail(nullptr, LBM_ERR_ARG, "reduce_every must be >= 0");
+
+    const int per[3] = {g->periodic[0] ? 1 : 0, g->periodic[1] ? 1 : 0, g->periodic[2] ? 1 : 0};
+    const int dims[3] = {nx, ny, nz};
+    const uint8_t *solid = g->solid;
+
+    // compact fluid index in voxel order (x fastest): streaming partners of a
+    // warp's nodes are then mostly contiguous too
+    std::vector<int32_t> cidx((size_t)nv, -1);
+    std::vector<uint32_t> pvox;
+    for (int64_t v = 0; v < nv; ++v)
+        if (!solid[v]) {
+            cidx[(size_t)v] = (int32_t)pvox.size();
+            pvox.push_back((uint32_t)v);
+        }
+    const int64_t N = (int64_t)pvox.size();
+    std::vector<uint8_t> nflags((size_t)N, 0);
+    auto face_bits = [&](const int c[3]) {
+        uint32_t f = 0;
+        if (per[0] && c[0] == 0) f |= F_XLO;
+        if (per[0] && c[0] == nx - 1) f |= F_XHI;
+        if (per[1] && c[1] == 0) f |= F_YLO;
+        if (per[1] && c[1] == ny - 1) f |= F_YHI;
+        if (per[2] && c[2] == 0) f |= F_ZLO;
+        if (per[2] && c[2] == nz - 1) f |= F_ZHI;
+        return f;
+    };
+    for (int64_t n = 0; n < N; ++n) {
+        const int64_t v = pvox[(size_t)n];
+        const int c[3] = {(int)(v % nx), (int)((v / nx) % ny), (int)(v / ((int64_t)nx * ny))};
+        uint32_t f = face_bits(c);
+        if (open_z && c[2] == 0) f |= F_INLET;
+        if (open_z && c[2] == nz - 1) f |= F_OUTLET;
+        nflags[(size_t)n] = (uint8_t)f;
+        for (int j = 1; j < 19; ++j) {
+            const int e[3] = {kEx[j], kEy[j], kEz[j]};
+            for (int a = 0; a < 3; ++a) {
+                const int m = c[a] + e[a];
+                if ((m < 0 || m >= dims[a]) && !per[a] && !(open_z && a == 2))
+                    return fail(nullptr, LBM_ERR_ARG, "a fluid voxel touches a closed (non-periodic, non-open) face");
+            }
+        }
+        if (open_z && (c[2] == 0 || c[2] == nz - 1)) {
+            const int64_t vi = v + (c[2] == 0 ? 1 : -1) * (int64_t)nx * ny;
+            if (solid[vi]) return fail(nullptr, LBM_ERR_ARG, "an open-plane fluid voxel has a solid interior neighbour");
+        }
+    }
+
+    // walls: solid voxels with at least one in-domain fluid neighbour (Eq. 15)
+    std::vector<uint32_t> wpvox, wmask;
+    std::vector<double> winv, wxi;
+    for (int64_t v = 0; v < nv; ++v) {
+        if (!solid[v]) continue;
+        const int c[3] = {(int)(v % nx), (int)((v / nx) % ny), (int)(v / ((int64_t)nx * ny))};
+        uint32_t mask = 0;
+        double den = 0;
+        for (int j = 1; j < 19; ++j) {
+            int m[3] = {c[0] + kEx[j], c[1] + kEy[j], c[2] + kEz[j]};
+            bool in = true;
+            for (int a = 0; a < 3; ++a) {
+                if (m[a] < 0 || m[a] >= dims[a]) {
+                    if (!per[a]) in = false;
+                    m[a] = (m[a] + dims[a]) % dims[a];
+                }
+            }
+            if (!in) continue;
+            const int64_t u = m[0] + (int64_t)nx * (m[1] + (int64_t)ny * m[2]);
+            if (!solid[u]) {
+                mask |= 1u << j;
+                den += weight(j);
+            }
+        }
+        if (!mask) continue;
+        wpvox.push_back((uint32_t)v);
+        wmask.push_back(mask | (face_bits(c) << kWallFaceShift));
+        winv.push_back(1.0 / den);
+        wxi.push_back(g->xi_field ? (double)g->xi_field[v] : p->xi);
+    }
+    const int64_t NW = (int64_t)wpvox.size();
+
+    lbm_ctx *c = new lbm_ctx();
+    cudaGetDevice(&c->device);
+    c->alloc_fn = g_alloc;
+    c->free_fn = g_free;
+    c->alloc_user = g_alloc_user;
+    c->nx = nx;
+    c->ny = ny;
+    c->nz = nz;
+    c->nv = nv;
+    for (int a = 0; a < 3; ++a) c->periodic[a] = per[a];
+    c->open_axis = g->open_axis;
+    c->p = *p;
+    c->storage = p->storage;
+    c->kernel = LBM_KERNEL_SPLIT;
+
+    const size_t sz = p->storage == LBM_STORE_FP64 ? 8 : 4;  // population storage bytes
+    const size_t szc = sz;                                     // compute-type bytes
+    const int64_t npad = ((N + 63) / 64) * 64 + 64;
+    const int nxy = nx * ny;
+    DevState &s = c->s;
+    s.npad = npad;
+    s.n_fluid = (int32_t)N;
+    s.nx = nx;
+    s.ny = ny;
+    s.nz = nz;
+    s.sx = nx;
+    s.sxy = nxy;
+    s.nv = nv;
+    s.n_wall = (int32_t)NW;
+    s.open_z = open_z ? 1 : 0;
+    s.nxy = nxy;
+    s.sample_lo = g->sample_lo;
+    s.sample_hi = g->sample_hi;
+    s.tau1 = p->tau[0];
+    s.tau2 = p->tau[1];
+    s.G = p->G;
+    s.gx = p->body_force[0];
+    s.gy = p->body_force[1];
+    s.gz = p->body_force[2];
+    s.rho_in1 = p->rho_in1;
+    s.rho_out2 = p->rho_out2;
+    s.rref1 = 0;
+    s.rref2 = 0;
+    s.velocity_shift = p->velocity_shift ? 1 : 0;
+
+    bool ok = true;
+    auto A = [&](size_t bytes) {
+        void *q = dalloc(c, bytes);
+        if (!q) ok = false;
+        return q;
+    };
+    s.f = A((size_t)2 * 19 * npad * sz);
+    void *d_pvox = A((size_t)N * 4);
+    void *d_nflags = A((size_t)N);
+    void *d_cidx = A((size_t)nv * 4);
+    s.psi = A((size_t)nv * 2 * szc);
+    void *d_wpvox = A((size_t)NW * 4);
+    void *d_wmask = A((size_t)NW * 4);
+    void *d_winv = A((size_t)NW * szc);
+    void *d_wxi = A((size_t)NW * szc);
+    if (open_z) {
+        s.bc = A((size_t)2 * 2 * 5 * nxy * sz);
+        c->d_frozen = (double *)A((size_t)2 * 5 * nxy * 8);
+    }
+    c->d_partials = (double *)A((size_t)kReduceBlocks * kReduceSlots * 8);
+    c->d_red = (double *)A((size_t)kReduceSlots * 8);
+    if (!ok) {
+        lbm_destroy(c);
+        return fail(nullptr, LBM_ERR_ALLOC, "device allocation failed");
+    }
+    s.pvox = (const uint32_t *)d_pvox;
+    s.nflags = (const uint8_t *)d_nflags;
+    s.cidx = (const int32_t *)d_cidx;
+    s.wpvox = (const uint32_t *)d_wpvox;
+    s.wmask = (const uint32_t *)d_wmask;
+    s.winv = d_winv;
+    s.wxi = d_wxi;
+    s.frozen = c->d_frozen;
+
+    std::vector<float> winv32, wxi32;
+    const void *winv_h = winv.data(), *wxi_h = wxi.data();
+    if (szc == 4) {
+        winv32.assign(winv.begin(), winv.end());
+        wxi32.assign(wxi.begin(), wxi.end());
+        winv_h = winv32.data();
+        wxi_h = wxi32.data();
+    }
+    cudaError_t e = cudaSuccess;
+    auto H2D = [&](void *dst, const void *src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    H2D(d_pvox, pvox.data(), (size_t)N * 4);
+    H2D(d_nflags, nflags.data(), (size_t)N);
+    H2D(d_cidx, cidx.data(), (size_t)nv * 4);
+    H2D(d_wpvox, wpvox.data(), (size_t)NW * 4);
+    H2D(d_wmask, wmask.data(), (size_t)NW * 4);
+    H2D(d_winv, winv_h, (size_t)NW * szc);
+    H2D(d_wxi, wxi_h, (size_t)NW * szc);
+    if (e == cudaSuccess) e = cudaMemset(s.f, 0, (size_t)2 * 19 * npad * sz);
+    if (e == cudaSuccess) e = cudaMemset(s.psi, 0, (size_t)nv * 2 * szc);
+    if (e == cudaSuccess && open_z) e = cudaMemset(s.bc, 0, (size_t)2 * 2 * 5 * nxy * sz);
+    if (e == cudaSuccess && open_z) e = cudaMemset(c->d_frozen, 0, (size_t)2 * 5 * nxy * 8);
+    if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->h_flag, sizeof(int), cudaHostAllocMapped);
+    if (e == cudaSuccess) {
+        *c->h_flag = 0;
+        e = cudaHostGetDevicePointer((void **)&c->d_flag, c->h_flag, 0);
+    }
+    if (e != cudaSuccess) {
+        lbm_destroy(c);
+        return fail(nullptr, LBM_ERR_CUDA, std::string("lbm_create: ") + cudaGetErrorString(e));
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    std::vector<void *> a = c->allocs;
+    for (void *q : a) dfree(c, q);
+    if (c->h_flag) cudaFreeHost(c->h_flag);
+    if (c->have_ev)
+        for (auto &ev : c->ev) cudaEventDestroy(ev);
+    delete c;
+}
+
+lbm_status lbm_init_densities(lbm_ctx *c, const double *rho1, const double *rho2)
+{
+    if (!c || !rho1 || !rho2) return LBM_ERR_ARG;
+    const size_t bytes = (size_t)c->nv * 8;
+    double *d = (double *)dalloc(c, 2 * bytes);
+    if (!d) return fail(c, LBM_ERR_ALLOC, "temporary density buffer");
+    cudaError_t e = cudaMemcpyAsync(d, rho1, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d + c->nv, rho2, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(c->stream);
+        dfree(c, d);
+        return cuda_fail(c, e, "lbm_init_densities");
+    }
+    dispatch(c, [&](auto tag) {
+        using TS = decltype(tag);
+        Ops<TS>::init_eq(c->s, d, c->stream);
+        Ops<TS>::capture_frozen(c->s, c->d_frozen, c->stream);
+    });
+    c->launches += 2;
+    c->step = 0;
+    lbm_status st = check_launch(c, "lbm_init_densities");
+    cudaStreamSynchronize(c->stream);
+    dfree(c, d);
+    if (st != LBM_OK) return st;
+    return capture_initial_mass(c);
+}
+
+lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
+{
+    if (!c || !f) return LBM_ERR_ARG;
+    const size_t bytes = (size_t)38 * c->nv * 8;
+    double *d = (double *)dalloc(c, bytes);
+    if (!d) return fail(c, LBM_ERR_ALLOC, "temporary population buffer");
+    cudaError_t e = cudaMemcpyAsync(d, f, bytes, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(c->stream);
+        dfree(c, d);
+        return cuda_fail(c, e, "lbm_set_populations");
+    }
+    dispatch(c, [&](auto tag) {
+        using TS = decltype(tag);
+        Ops<TS>::scatter(c->s, d, c->stream);
+        Ops<TS>::capture_frozen(c->s, c->d_frozen, c->stream);
+    });
+    c->launches += 2;
+    c->step = 0;
+    lbm_status st = check_launch(c, "lbm_set_populations");
+    cudaStreamSynchronize(c->stream);
+    dfree(c, d);
+    if (st != LBM_OK) return st;
+    return capture_initial_mass(c);
+}
+
+lbm_status lbm_get_populations(lbm_ctx *c, double *f)
+{
+    if (!c || !f) return LBM_ERR_ARG;
+    const size_t bytes = (size_t)38 * c->nv * 8;
+    double *d = (double *)dalloc(c, bytes);
+    if (!d) return fail(c, LBM_ERR_ALLOC, "temporary population buffer");
+    cudaError_t e = cudaMemsetAsync(d, 0, bytes, c->stream);
+    dispatch(c, [&](auto tag) {
+        using TS = decltype(tag);
+        Ops<TS>::gather(c->s, (int)(c->step & 1), d, c->stream);
+    });
+    c->launches += 1;
+    lbm_status st = check_launch(c, "lbm_get_populations");
+    if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, bytes, cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    dfree(c, d);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_get_populations");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "lbm_get_populations");
+    return st != LBM_OK ? st : device_status(c);
+}
+
+lbm_status lbm_step(lbm_ctx *c, int64_t n)
+{
+    if (!c || n < 0) return LBM_ERR_ARG;
+    for (int64_t k = 0; k < n; ++k) enqueue_step(c, nullptr);
+    lbm_status st = check_launch(c, "lbm_step");
+    return st != LBM_OK ? st : device_status(c);
+}
+
+lbm_status lbm_step_timed(lbm_ctx *c, int64_t n, double *kernel_ms, int32_t nk)
+{
+    if (!c || n < 0 || (nk > 0 && !kernel_ms)) return LBM_ERR_ARG;
+    if (!c->have_ev) {
+        for (auto &ev : c->ev) cudaEventCreate(&ev);
+        c->have_ev = true;
+    }
+    for (int64_t k = 0; k < n; ++k) {
+        enqueue_step(c, c->ev);
+        cudaError_t e = cudaEventSynchronize(c->ev[4]);
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_timed");
+        for (int q = 0; q < 4 && q < nk; ++q) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, c->ev[q], c->ev[q + 1]);
+            kernel_ms[q] += ms;
+        }
+    }
+    lbm_status st = check_launch(c, "lbm_step_timed");
+    return st != LBM_OK ? st : device_status(c);
+}
+
+lbm_status lbm_read_fields(lbm_ctx *c, uint32_t mask, double *out, size_t n_per_field)
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    if (n_per_field < (size_t)c->nv) return fail(c, LBM_ERR_ARG, "n_per_field is smaller than nx*ny*nz");
+    const size_t bytes = (size_t)6 * c->nv * 8;
+    double *d = (double *)dalloc(c, bytes);
+    if (!d) return fail(c, LBM_ERR_ALLOC, "temporary field buffer");
+    cudaError_t e = cudaMemsetAsync(d, 0, bytes, c->stream);
+    const int par = (int)(c->step & 1);
+    dispatch(c, [&](auto tag) {
+        using TS = decltype(tag);
+        Ops<TS>::dens(c->s, par, c->stream);
+        Ops<TS>::wall(c->s, c->stream);
+        Ops<TS>::fields(c->s, par, d, c->stream);
+    });
+    c->launches += 3;
+    lbm_status st = check_launch(c, "lbm_read_fields");
+    int k = 0;
+    for (int b = 0; b < 6; ++b) {
+        if (!(mask & (1u << b))) continue;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(out + (size_t)k * n_per_field, d + (size_t)b * c->nv, (size_t)c->nv * 8,
+                                cudaMemcpyDeviceToHost, c->stream);
+        ++k;
+    }
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    dfree(c, d);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_read_fields");
+    if (e2 != cudaSuccess) return cuda_fail(c, e2, "lbm_read_fields");
+    return st != LBM_OK ? st : device_status(c);
+}
+
+lbm_status lbm_saturation(lbm_ctx *c, double out[4])
+{
+    if (!c || !out) return LBM_ERR_ARG;
+    run_reduce(c);
+    lbm_status st = check_launch(c, "lbm_saturation");
+    double red[kReduceSlots];
+    cudaError_t e = cudaMemcpyAsync(red, c->d_red, sizeof(red), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_saturation");
+    out[0] = red[2] > 0 ? red[3] / red[2] : 0.0;
+    out[1] = red[2] > 0 ? red[4] / red[2] : 0.0;
+    out[2] = red[0];
+    out[3] = red[1];
+    return st != LBM_OK ? st : device_status(c);
+}
+
+lbm_status lbm_set_inlet(lbm_ctx *c, double rho_in1)
+{
+    if (!c) return LBM_ERR_ARG;
+    c->p.rho_in1 = rho_in1;
+    c->s.rho_in1 = rho_in1;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_stream(lbm_ctx *c, void *stream)
+{
+    if (!c) return LBM_ERR_ARG;
+    c->stream = (cudaStream_t)stream;
+    return LBM_OK;
+}
+
+lbm_status lbm_synchronize(lbm_ctx *c)
+{
+    if (!c) return LBM_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        c->sticky = LBM_ERR_CUDA;
+        return cuda_fail(c, e, "lbm_synchronize");
+    }
+    return device_status(c);
+}
+
+lbm_status lbm_get_info(const lbm_ctx *c, lbm_info *info)
+{
+    if (!c || !info) return LBM_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    info->n_fluid = c->s.n_fluid;
+    info->n_wall = c->s.n_wall;
+    info->n_voxels = c->nv;
+    info->step = c->step;
+    info->device_bytes = c->bytes;
+    info->launches = c->launches;
+    info->storage = c->storage;
+    info->kernel = c->kernel;
+    return LBM_OK;
+}
+
+const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+}  // extern "C"

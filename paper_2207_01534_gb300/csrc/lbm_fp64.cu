@@ -1,0 +1,7 @@
+// FP64 populations, FP64 arithmetic.
+#include "lbm_kernels.cuh"
+#include "lbm_ops.inl"
+
+namespace lbm {
+template struct Ops<double>;
+}

@@ -1,0 +1,81 @@
+// lbm_internal.h -- device state shared by the host API and the kernel
+// translation units of liblbm.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Node flag bits (uint8 per fluid node; bits 24..29 of a wall's mask word use
+// the same face bits shifted by 24).  A periodic-face bit means the neighbour
+// across that face wraps to the opposite face.  INLET / OUTLET mark the nodes
+// of the z = 0 and z = nz-1 open planes.
+enum : uint32_t {
+    F_XLO = 1u, F_XHI = 2u, F_YLO = 4u, F_YHI = 8u, F_ZLO = 16u, F_ZHI = 32u,
+    F_INLET = 64u, F_OUTLET = 128u
+};
+constexpr uint32_t kFaceMask = 63u;
+constexpr int kWallFaceShift = 24;
+
+// Everything a kernel needs, passed by value.
+struct DevState {
+    // populations: storage type, [sigma][i][Npad], SoA
+    void *f;
+    int64_t npad;            // stride between direction arrays (multiple of 64)
+    int32_t n_fluid;
+    const uint32_t *pvox;    // [n_fluid] voxel index v = x + nx*(y + ny*z)
+    const uint8_t *nflags;   // [n_fluid]
+    const int32_t *cidx;     // [nv] compact index of a fluid voxel, -1 solid
+    void *psi;               // [nv] pairs (psi1, psi2) in the compute type
+    int32_t nx, ny, nz;
+    int32_t sx, sxy;         // strides nx, nx*ny
+    int64_t nv;
+    // walls (solid voxels with at least one fluid neighbour)
+    int32_t n_wall;
+    const uint32_t *wpvox;   // [n_wall]
+    const uint32_t *wmask;   // [n_wall] bit i: direction i leads to an in-domain fluid voxel; face bits << 24
+    const void *winv;        // [n_wall] 1 / sum of w_i over those directions (Eq. 15 denominator), compute type
+    const void *wxi;         // [n_wall] xi at the wall voxel, compute type
+    // open planes (z): bc slots hold the missing populations of the odd-parity layout,
+    // [plane][sigma][k][nxy] in the storage type; frozen holds the initial values of
+    // the non-prescribed component's missing populations, [plane][k][nxy] (double).
+    int32_t open_z;
+    void *bc;
+    const double *frozen;
+    int32_t nxy;
+    // sample slab for saturation
+    int32_t sample_lo, sample_hi;
+    // model parameters
+    double tau1, tau2, G, gx, gy, gz, rho_in1, rho_out2;
+    double rref1, rref2;
+    int32_t velocity_shift;
+};
+
+// Per-storage-type kernel launchers, explicitly instantiated in one
+// translation unit per storage type.
+template <typename TS>
+struct Ops {
+    static void dens(const DevState &s, int parity, cudaStream_t st);
+    static void wall(const DevState &s, cudaStream_t st);
+    static void fused(const DevState &s, int parity, cudaStream_t st);
+    static void plane(const DevState &s, int parity_next, cudaStream_t st);
+    // rest equilibrium from device densities rho[2][nv] (double); parity-0 layout
+    static void init_eq(const DevState &s, const double *rho, cudaStream_t st);
+    // populations [2][19][nv] (double, device) -> parity-0 layout
+    static void scatter(const DevState &s, const double *f, cudaStream_t st);
+    // current layout -> populations [2][19][nv] (double, device); solids untouched
+    static void gather(const DevState &s, int parity, double *f, cudaStream_t st);
+    // capture the frozen missing populations from the parity-0 layout
+    static void capture_frozen(const DevState &s, double *frozen, cudaStream_t st);
+    // fields (rho1, rho2, ux, uy, uz, P) [6][nv] (double, device); needs dens+wall first
+    static void fields(const DevState &s, int parity, double *out, cudaStream_t st);
+    // FP64 reduction over psi (needs dens first): partials[nblocks][8] then out[8]
+    static void reduce(const DevState &s, double *partials, int nblocks, double *out, cudaStream_t st);
+};
+
+constexpr int kReduceBlocks = 1024;
+constexpr int kReduceThreads = 256;
+constexpr int kReduceSlots = 8;  // m1, m2, count, nw, smooth, nonfinite, unused, unused
+
+}  // namespace lbm

@@ -1,0 +1,84 @@
+// lbm_ops.inl -- launchers of the split-schedule kernels for one storage type.
+// Included by lbm_fp32.cu / lbm_fp64.cu after lbm_kernels.cuh.
+#pragma once
+
+namespace lbm {
+
+static inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
+
+template <typename TS>
+void Ops<TS>::dens(const DevState &s, int parity, cudaStream_t st)
+{
+    if (s.n_fluid == 0) return;
+    if (parity) k_dens<TS, 1><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s);
+    else k_dens<TS, 0><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s);
+}
+
+template <typename TS>
+void Ops<TS>::wall(const DevState &s, cudaStream_t st)
+{
+    if (s.n_wall == 0) return;
+    k_wall<TS><<<grid_for(s.n_wall, 256), 256, 0, st>>>(s);
+}
+
+template <typename TS>
+void Ops<TS>::fused(const DevState &s, int parity, cudaStream_t st)
+{
+    if (s.n_fluid == 0) return;
+    if (parity) k_fused<TS, 1><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s);
+    else k_fused<TS, 0><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s);
+}
+
+template <typename TS>
+void Ops<TS>::plane(const DevState &s, int parity_next, cudaStream_t st)
+{
+    if (!s.open_z || s.nxy == 0) return;
+    if (parity_next) k_plane<TS, 1><<<grid_for(2LL * s.nxy, 128), 128, 0, st>>>(s);
+    else k_plane<TS, 0><<<grid_for(2LL * s.nxy, 128), 128, 0, st>>>(s);
+}
+
+template <typename TS>
+void Ops<TS>::init_eq(const DevState &s, const double *rho, cudaStream_t st)
+{
+    if (s.n_fluid == 0) return;
+    k_init_eq<TS><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, rho);
+}
+
+template <typename TS>
+void Ops<TS>::scatter(const DevState &s, const double *f, cudaStream_t st)
+{
+    if (s.n_fluid == 0) return;
+    k_scatter<TS><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, f);
+}
+
+template <typename TS>
+void Ops<TS>::gather(const DevState &s, int parity, double *f, cudaStream_t st)
+{
+    if (s.n_fluid == 0) return;
+    if (parity) k_gather<TS, 1><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, f);
+    else k_gather<TS, 0><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, f);
+}
+
+template <typename TS>
+void Ops<TS>::capture_frozen(const DevState &s, double *frozen, cudaStream_t st)
+{
+    if (!s.open_z || s.nxy == 0) return;
+    k_capture_frozen<TS><<<grid_for(2LL * s.nxy, 128), 128, 0, st>>>(s, frozen);
+}
+
+template <typename TS>
+void Ops<TS>::fields(const DevState &s, int parity, double *out, cudaStream_t st)
+{
+    if (s.n_fluid == 0) return;
+    if (parity) k_fields<TS, 1><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, out);
+    else k_fields<TS, 0><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, out);
+}
+
+template <typename TS>
+void Ops<TS>::reduce(const DevState &s, double *partials, int nblocks, double *out, cudaStream_t st)
+{
+    k_reduce<TS><<<nblocks, kReduceThreads, 0, st>>>(s, partials);
+    k_reduce_final<<<1, kReduceThreads, 0, st>>>(partials, nblocks, out);
+}
+
+}  // namespace lbm

@@ -1,0 +1,242 @@
+"""Python binding of liblbm (include/lbm.h): argument marshalling only.
+
+Every step of the method runs in the CUDA library.  PyTorch supplies the CUDA
+stream and, optionally, device memory (through its caching allocator).  If the
+library cannot be loaded this module raises: there is no CPU fallback.
+
+Arrays are numpy, shape (nz, ny, nx) (x fastest), like the geometry
+generators in ``inputs``; populations are (2, 19, nz, ny, nx).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK = 0
+STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_ALLOC", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_NONFINITE",
+          -5: "LBM_ERR_DRIFT", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_UNSUPPORTED"}
+STORAGE = {"fp32": 0, "fp64": 1, "fp16dev": 2, "bf16dev": 3}
+KERNEL = {"auto": 0, "split": 1, "fused": 2}
+FIELDS = ("rho1", "rho2", "ux", "uy", "uz", "P")
+
+
+class LbmError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s: %s" % (STATUS.get(code, code), msg))
+        self.code = code
+
+
+class Geometry(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32),
+                ("solid", ctypes.c_void_p), ("periodic", ctypes.c_int32 * 3), ("open_axis", ctypes.c_int32),
+                ("sample_lo", ctypes.c_int32), ("sample_hi", ctypes.c_int32), ("xi_field", ctypes.c_void_p)]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_double * 2), ("G", ctypes.c_double), ("xi", ctypes.c_double),
+                ("rho_in1", ctypes.c_double), ("rho_out2", ctypes.c_double), ("body_force", ctypes.c_double * 3),
+                ("bc", ctypes.c_int32), ("storage", ctypes.c_int32), ("velocity_shift", ctypes.c_int32),
+                ("reduce_every", ctypes.c_int32), ("rho_ref", ctypes.c_double * 2), ("kernel", ctypes.c_int32),
+                ("drift_limit", ctypes.c_double)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_fluid", ctypes.c_int64), ("n_wall", ctypes.c_int64), ("n_voxels", ctypes.c_int64),
+                ("step", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("launches", ctypes.c_int64),
+                ("storage", ctypes.c_int32), ("kernel", ctypes.c_int32)]
+
+
+_lib = None
+_ALLOC_CB = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE_CB = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+_torch_hooks = None
+
+
+def load(build_if_missing: bool = True):
+    """Load liblbm.so (building it in-tree first if needed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_missing and (not os.path.exists(path) or _build._stale()):
+        _build.build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    lib.lbm_default_params.argtypes = [ctypes.POINTER(Params)]
+    lib.lbm_create.argtypes = [ctypes.POINTER(Geometry), ctypes.POINTER(Params), ctypes.POINTER(P)]
+    lib.lbm_destroy.argtypes = [P]
+    lib.lbm_destroy.restype = None
+    lib.lbm_set_allocator.argtypes = [P, P, P]
+    lib.lbm_init_densities.argtypes = [P, P, P]
+    lib.lbm_set_populations.argtypes = [P, P]
+    lib.lbm_get_populations.argtypes = [P, P]
+    lib.lbm_step.argtypes = [P, ctypes.c_int64]
+    lib.lbm_step_timed.argtypes = [P, ctypes.c_int64, P, ctypes.c_int32]
+    lib.lbm_read_fields.argtypes = [P, ctypes.c_uint32, P, ctypes.c_size_t]
+    lib.lbm_saturation.argtypes = [P, P]
+    lib.lbm_set_inlet.argtypes = [P, ctypes.c_double]
+    lib.lbm_set_stream.argtypes = [P, P]
+    lib.lbm_synchronize.argtypes = [P]
+    lib.lbm_get_info.argtypes = [P, ctypes.POINTER(Info)]
+    lib.lbm_last_error.argtypes = [P]
+    lib.lbm_last_error.restype = ctypes.c_char_p
+    for name in ("lbm_default_params", "lbm_create", "lbm_set_allocator", "lbm_init_densities",
+                 "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_step_timed", "lbm_read_fields",
+                 "lbm_saturation", "lbm_set_inlet", "lbm_set_stream", "lbm_synchronize", "lbm_get_info"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def use_torch_allocator(enable: bool = True) -> None:
+    """Route later context allocations through PyTorch's caching allocator."""
+    global _torch_hooks
+    lib = load()
+    if not enable:
+        lib.lbm_set_allocator(None, None, None)
+        _torch_hooks = None
+        return
+    import torch
+
+    def _alloc(nbytes, _user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), torch.cuda.current_device()))
+        except Exception:  # reported to the library as an allocation failure
+            return None
+
+    def _free(ptr, _user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    a, f = _ALLOC_CB(_alloc), _FREE_CB(_free)
+    _torch_hooks = (a, f)  # keep the callbacks alive
+    lib.lbm_set_allocator(ctypes.cast(a, ctypes.c_void_p), ctypes.cast(f, ctypes.c_void_p), None)
+
+
+def _check(code, ctx=None):
+    if code != LBM_OK:
+        lib = load()
+        msg = lib.lbm_last_error(ctx)
+        raise LbmError(code, msg.decode() if msg else "")
+
+
+class Lattice:
+    """One simulation context (``lbm_ctx``) on the current CUDA device."""
+
+    def __init__(self, solid, tau=(1.0, 1.0), G=3.5, xi=0.0, xi_field=None, periodic=(1, 1, 1), open_axis=-1,
+                 rho_in1=1.0, rho_out2=1.0, body_force=(0.0, 0.0, 0.0), velocity_shift=1, storage="fp32",
+                 kernel="auto", sample=(0, 0), reduce_every=0, drift_limit=1e-6, rho_ref=(0.0, 0.0), stream=None):
+        lib = load()
+        self._lib = lib
+        solid = np.ascontiguousarray(solid, dtype=np.uint8)
+        assert solid.ndim == 3
+        self.shape = solid.shape
+        nz, ny, nx = solid.shape
+        self.nv = nx * ny * nz
+        g = Geometry()
+        g.nx, g.ny, g.nz = nx, ny, nz
+        g.solid = solid.ctypes.data
+        for a in range(3):
+            g.periodic[a] = int(bool(periodic[a]))
+        g.open_axis = int(open_axis)
+        g.sample_lo, g.sample_hi = int(sample[0]), int(sample[1])
+        xf = None
+        if xi_field is not None:
+            xf = np.ascontiguousarray(xi_field, dtype=np.float32)
+            assert xf.shape == solid.shape
+            g.xi_field = xf.ctypes.data
+        p = Params()
+        lib.lbm_default_params(ctypes.byref(p))
+        p.tau[0], p.tau[1] = float(tau[0]), float(tau[1])
+        p.G = float(G)
+        p.xi = float(xi)
+        p.rho_in1, p.rho_out2 = float(rho_in1), float(rho_out2)
+        for a in range(3):
+            p.body_force[a] = float(body_force[a])
+        p.velocity_shift = int(velocity_shift)
+        p.storage = STORAGE[storage]
+        p.kernel = KERNEL[kernel]
+        p.reduce_every = int(reduce_every)
+        p.drift_limit = float(drift_limit)
+        p.rho_ref[0], p.rho_ref[1] = float(rho_ref[0]), float(rho_ref[1])
+        h = ctypes.c_void_p()
+        _check(lib.lbm_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h)))
+        self._h = h
+        if stream is None:
+            try:
+                import torch
+
+                if torch.cuda.is_available():
+                    stream = torch.cuda.current_stream().cuda_stream
+            except ImportError:
+                stream = None
+        if stream:
+            _check(lib.lbm_set_stream(h, ctypes.c_void_p(int(stream))), h)
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self._lib.lbm_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _c(self, code):
+        _check(code, self._h)
+
+    def set_stream(self, stream):
+        self._c(self._lib.lbm_set_stream(self._h, ctypes.c_void_p(int(stream))))
+
+    def init_densities(self, rho1, rho2):
+        r1 = np.ascontiguousarray(np.broadcast_to(rho1, self.shape), dtype=np.float64)
+        r2 = np.ascontiguousarray(np.broadcast_to(rho2, self.shape), dtype=np.float64)
+        self._c(self._lib.lbm_init_densities(self._h, r1.ctypes.data, r2.ctypes.data))
+
+    def set_populations(self, f1, f2):
+        f = np.ascontiguousarray(np.stack([np.asarray(f1).reshape((19,) + self.shape),
+                                           np.asarray(f2).reshape((19,) + self.shape)]), dtype=np.float64)
+        self._c(self._lib.lbm_set_populations(self._h, f.ctypes.data))
+
+    def get_populations(self):
+        f = np.zeros((2, 19) + self.shape)
+        self._c(self._lib.lbm_get_populations(self._h, f.ctypes.data))
+        return f[0], f[1]
+
+    def step(self, n: int = 1):
+        self._c(self._lib.lbm_step(self._h, int(n)))
+
+    def step_timed(self, n: int = 1):
+        """Run n steps; return per-kernel device milliseconds (dens, wall, fused, plane, pipeline)."""
+        ms = np.zeros(5)
+        self._c(self._lib.lbm_step_timed(self._h, int(n), ms.ctypes.data, 5))
+        return ms
+
+    def fields(self, names=FIELDS):
+        mask = 0
+        for nme in names:
+            mask |= 1 << FIELDS.index(nme)
+        order = [nme for nme in FIELDS if mask & (1 << FIELDS.index(nme))]
+        out = np.zeros((len(order), self.nv))
+        self._c(self._lib.lbm_read_fields(self._h, mask, out.ctypes.data, self.nv))
+        return {nme: out[k].reshape(self.shape) for k, nme in enumerate(order)}
+
+    def saturation(self):
+        """(S_w, smooth S_nw, mass1, mass2)."""
+        out = np.zeros(4)
+        self._c(self._lib.lbm_saturation(self._h, out.ctypes.data))
+        return tuple(float(x) for x in out)
+
+    def set_inlet(self, rho_in1: float):
+        self._c(self._lib.lbm_set_inlet(self._h, float(rho_in1)))
+
+    def synchronize(self):
+        self._c(self._lib.lbm_synchronize(self._h))
+
+    def info(self) -> dict:
+        i = Info()
+        self._c(self._lib.lbm_get_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in Info._fields_}

@@ -1,0 +1,242 @@
+"""GPU path vs the FP64 oracle on the same seeded inputs, through the C ABI.
+
+Tolerances:
+  * FP32 path after 1000 steps: max |rho_gpu - rho_oracle| / max |rho_oracle|
+    <= 1e-5 per component, and relative mass drift <= 1e-6 on closed domains;
+  * FP64 path: 1e-12 on the same measure (only the summation order differs);
+  * a few steps from a random non-equilibrium state: every population, FP64
+    to 1e-13 absolute, FP32 to 2e-6 absolute (populations are O(0.1)).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2207_01534_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32_RHO = 1e-5
+TOL_FP64_RHO = 1e-12
+TOL_MASS = 1e-6
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    assert torch.cuda.is_available(), "these tests need a GPU"
+    from paper_2207_01534_gb300 import lbm as m
+
+    m.load()
+    return m
+
+
+def _pair(lbm, solid, storage="fp32", **kw):
+    g = lbm.Lattice(solid, storage=storage, **kw)
+    o = oracle.Oracle(solid, **{k: v for k, v in kw.items() if k not in ("sample",)})
+    return g, o
+
+
+def _rel_linf(a, b):
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+def _compare_rho(g, o, tol):
+    fg = g.fields(("rho1", "rho2"))
+    fo = o.fields()
+    e1 = _rel_linf(fg["rho1"], fo["rho1"])
+    e2 = _rel_linf(fg["rho2"], fo["rho2"])
+    assert e1 <= tol and e2 <= tol, (e1, e2)
+    return e1, e2
+
+
+def _porous_periodic(n=(22, 18, 20), seed=7):
+    nz, ny, nx = n
+    rng = np.random.default_rng(seed)
+    zz, yy, xx = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+    solid = np.zeros(n, np.uint8)
+    for _ in range(6):
+        c = rng.uniform(0, 1, 3) * np.array([nx, ny, nz])
+        r = rng.uniform(2.0, 3.5)
+        d2 = np.zeros(n)
+        for ax, (L, crd) in enumerate(((nx, xx), (ny, yy), (nz, zz))):
+            d = np.abs(crd - c[ax])
+            d = np.minimum(d, L - d)
+            d2 += d * d
+        solid[d2 <= r * r] = 1
+    return solid
+
+
+@pytest.mark.parametrize("storage,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+@pytest.mark.parametrize("steps", [1, 2, 5])
+def test_random_state_all_populations(lbm, storage, tol, steps):
+    """Every population after a few steps from a random non-equilibrium state,
+    on a periodic porous domain with walls (both A-A parities)."""
+    solid = _porous_periodic()
+    f1, f2 = inputs.random_pops_state(solid, inputs.SEED_BASE + 100, rho_lo=0.05, rho_hi=0.9, noise=0.05)
+    kw = dict(tau=(1.7, 0.62), G=3.5, xi=-0.3)
+    g, o = _pair(lbm, solid, storage, **kw)
+    g.set_populations(f1, f2)
+    o.set_pops(f1, f2)
+    g.step(steps)
+    o.step(steps)
+    a1, a2 = g.get_populations()
+    b1, b2 = o.get_pops()
+    assert np.abs(a1 - b1).max() <= tol and np.abs(a2 - b2).max() <= tol
+
+
+def test_populations_round_trip_fp64(lbm):
+    solid = _porous_periodic()
+    f1, f2 = inputs.random_pops_state(solid, inputs.SEED_BASE + 101)
+    g = lbm.Lattice(solid, storage="fp64")
+    g.set_populations(f1, f2)
+    a1, a2 = g.get_populations()
+    assert np.array_equal(a1, f1) and np.array_equal(a2, f2)
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", TOL_FP32_RHO), ("fp64", TOL_FP64_RHO)])
+def test_laplace_48_thousand_steps(lbm, storage, tol):
+    """48^3 periodic droplet (R = 10, W = 5, densities 1.0 / 0.03, tau = 1,
+    G = 3.5), 1000 steps: densities and pressure jump."""
+    solid, r1, r2 = inputs.laplace_48()
+    g, o = _pair(lbm, solid, storage, tau=(1.0, 1.0), G=3.5)
+    g.init_densities(r1, r2)
+    o.init_densities(r1, r2)
+    m0 = g.saturation()
+    g.step(1000)
+    o.step(1000)
+    _compare_rho(g, o, tol)
+    m1 = g.saturation()
+    assert abs(m1[2] - m0[2]) / m0[2] <= TOL_MASS and abs(m1[3] - m0[3]) / m0[3] <= TOL_MASS
+    fg, fo = g.fields(), o.fields()
+    dpg = fg["P"][24, 24, 24] - fg["P"][0, 0, 0]
+    dpo = fo["P"][24, 24, 24] - fo["P"][0, 0, 0]
+    assert abs(dpg - dpo) <= 10 * tol * abs(fo["P"]).max()
+    for k in ("ux", "uy", "uz"):
+        assert np.abs(fg[k] - fo[k]).max() <= 10 * tol
+
+
+def _open_porous(n=(30, 16, 14), seed=11, res=4):
+    solid = _porous_periodic(n, seed)
+    solid[:res] = 0
+    solid[-res:] = 0
+    return solid
+
+
+@pytest.mark.parametrize("storage,tol", [("fp32", TOL_FP32_RHO), ("fp64", TOL_FP64_RHO)])
+def test_open_drainage_porous(lbm, storage, tol):
+    """Drainage through a porous slab with NEEM inlet/outlet, frozen missing
+    populations, mirrored pseudopotential at the planes, theta = 45 deg, M = 10."""
+    solid = _open_porous()
+    r1, r2 = inputs.drainage_init(solid, 4)
+    kw = dict(tau=inputs.tau_for_viscosity_ratio(10.0), G=3.5, xi=inputs.xi_of_theta(45.0), periodic=(1, 1, 0),
+              open_axis=2, rho_in1=1.08, rho_out2=1.0)
+    g, o = _pair(lbm, solid, storage, **kw)
+    g.init_densities(r1, r2)
+    o.init_densities(r1, r2)
+    for chunk in (1, 1, 98, 300):  # odd and even step counts
+        g.step(chunk)
+        o.step(chunk)
+        _compare_rho(g, o, tol)
+    fg = g.fields(("rho1", "rho2"))
+    fl = solid == 0
+    assert np.abs(fg["rho1"][0][fl[0]] - 1.08).max() < 1e-5
+    assert np.abs(fg["rho2"][-1][fl[-1]] - 1.0).max() < 1e-5
+    a1, a2 = g.get_populations()
+    b1, b2 = o.get_pops()
+    assert np.abs(a1 - b1).max() < 10 * tol and np.abs(a2 - b2).max() < 10 * tol
+
+
+def test_walled_lateral_faces_and_xi_field(lbm):
+    """Non-periodic x closed by solid faces, per-voxel xi field, open z."""
+    nz, ny, nx = 24, 10, 12
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    solid[:, :, 0] = 1
+    solid[:, :, -1] = 1
+    solid[8:14, 3:7, 4:8] = 1
+    rng = np.random.default_rng(5)
+    xi = rng.uniform(-0.4, 0.3, solid.shape)
+    r1, r2 = inputs.drainage_init(solid, 3)
+    kw = dict(tau=(1.1, 0.62), G=3.5, xi_field=xi, periodic=(0, 1, 0), open_axis=2, rho_in1=1.05, rho_out2=1.0)
+    g, o = _pair(lbm, solid, "fp64", **kw)
+    g.init_densities(r1, r2)
+    o.init_densities(r1, r2)
+    g.step(301)
+    o.step(301)
+    _compare_rho(g, o, TOL_FP64_RHO)
+
+
+def test_body_force_and_no_shift(lbm):
+    """Body force with the printed Eq. 8 momenta (velocity_shift = 0)."""
+    solid = _porous_periodic((12, 10, 14), 3)
+    r1, r2 = inputs.droplet_densities(solid.shape, (7, 5, 6), 3.0, 3.0, 1.0, 0.03)
+    fl = solid == 0
+    kw = dict(tau=(1.0, 1.0), G=3.0, xi=0.1, body_force=(1e-5, -2e-5, 3e-5), velocity_shift=0)
+    g, o = _pair(lbm, solid, "fp64", **kw)
+    g.init_densities(r1 * fl, r2 * fl)
+    o.init_densities(r1 * fl, r2 * fl)
+    g.step(50)
+    o.step(50)
+    _compare_rho(g, o, TOL_FP64_RHO)
+
+
+def test_saturation_matches_oracle(lbm):
+    solid = _open_porous()
+    r1, r2 = inputs.drainage_init(solid, 4)
+    kw = dict(tau=(1.7, 0.62), G=3.5, xi=-0.3, periodic=(1, 1, 0), open_axis=2, rho_in1=1.1, rho_out2=1.0)
+    g = lbm.Lattice(solid, storage="fp64", sample=(4, 26), **kw)
+    o = oracle.Oracle(solid, **kw)
+    g.init_densities(r1, r2)
+    o.init_densities(r1, r2)
+    g.step(200)
+    o.step(200)
+    sg = g.saturation()
+    so = o.saturation(4, 26)
+    fo = o.fields()
+    fl = (solid == 0)
+    fl[:4] = False
+    fl[26:] = False
+    d = (fo["rho2"] - fo["rho1"])[fl]
+    lo_cnt, hi_cnt = (d > 1e-9).sum() / fl.sum(), (d > -1e-9).sum() / fl.sum()
+    assert lo_cnt <= sg[0] <= hi_cnt
+    assert abs(sg[1] - so[1]) < 1e-12 and abs(sg[2] - so[2]) < 1e-10 * so[2] and abs(sg[3] - so[3]) < 1e-10 * so[3]
+
+
+def test_degenerate_domains(lbm):
+    # a single periodic fluid voxel: every neighbour is itself
+    solid = np.zeros((1, 1, 1), np.uint8)
+    g, o = _pair(lbm, solid, "fp64", tau=(1.2, 0.8), G=3.5)
+    g.init_densities(np.full((1, 1, 1), 0.7), np.full((1, 1, 1), 0.3))
+    o.init_densities(0.7, 0.3)
+    g.step(7)
+    o.step(7)
+    _compare_rho(g, o, TOL_FP64_RHO)
+    # a quasi-1D column with a flat interface
+    solid = np.zeros((40, 1, 1), np.uint8)
+    z = np.arange(40)[:, None, None]
+    r1 = np.where((z > 10) & (z < 30), 1.0, 0.03) + 0 * solid
+    r2 = np.where((z > 10) & (z < 30), 0.03, 1.0) + 0 * solid
+    g, o = _pair(lbm, solid, "fp32", tau=(1.0, 1.0), G=3.5)
+    g.init_densities(r1, r2)
+    o.init_densities(r1, r2)
+    g.step(1000)
+    o.step(1000)
+    _compare_rho(g, o, TOL_FP32_RHO)
+    # no fluid at all
+    g = lbm.Lattice(np.ones((4, 4, 4), np.uint8))
+    g.init_densities(np.zeros((4, 4, 4)), np.zeros((4, 4, 4)))
+    g.step(3)
+    assert g.saturation() == (0.0, 0.0, 0.0, 0.0)
+
+
+def test_ragged_sizes_span_many_blocks(lbm):
+    """A size that is not a multiple of the block size, with both parities."""
+    solid = _porous_periodic((17, 23, 29), 9)
+    r1, r2 = inputs.droplet_densities(solid.shape, (14, 11, 8), 5.0, 4.0, 1.0, 0.03)
+    fl = solid == 0
+    g, o = _pair(lbm, solid, "fp32", tau=(1.7, 0.62), G=3.5, xi=0.2)
+    g.init_densities(r1 * fl, r2 * fl)
+    o.init_densities(r1 * fl, r2 * fl)
+    g.step(333)
+    o.step(333)
+    _compare_rho(g, o, TOL_FP32_RHO)

@@ -255,8 +255,14 @@ __device__ __forceinline__ void collide(C f[2][19], C rho1, C rho2, C inv_rho, c
     const C uF1 = u[0] * F1[0] + u[1] * F1[1] + u[2] * F1[2];
     const C uF2 = u[0] * F2[0] + u[1] * F2[1] + u[2] * F2[2];
     const C rho[2] = {rho1, rho2};
+    // The rest population is written last as rho^sigma minus the 18 moving
+    // post-collision populations.  In exact arithmetic this equals Eq. 1 for
+    // i = 0 (sum_i f^eq_i = rho, sum_i S_i = 0); in FP32 it removes the mass
+    // bias of the rounded weights (their FP32 sum exceeds 1 by ~1.5e-8, which
+    // would otherwise create mass at every collision).
+    C sum1 = 0, sum2 = 0;
 #pragma unroll
-    for (int i = 0; i < 19; ++i) {
+    for (int i = 1; i < 19; ++i) {
         const C eu = ex(i) * u[0] + ey(i) * u[1] + ez(i) * u[2];
         const C base = C(1) + C(3) * eu + C(4.5) * eu * eu - usq;
         const C eF1 = ex(i) * F1[0] + ey(i) * F1[1] + ez(i) * F1[2];
@@ -268,7 +274,11 @@ __device__ __forceinline__ void collide(C f[2][19], C rho1, C rho2, C inv_rho, c
         const C fe2 = w * rho[1] * base;
         f[0][i] = f[0][i] - om * (f[0][i] - fe1) + cf * S1;
         f[1][i] = f[1][i] - om * (f[1][i] - fe2) + cf * S2;
+        sum1 += f[0][i];
+        sum2 += f[1][i];
     }
+    f[0][0] = rho1 - sum1;
+    f[1][0] = rho2 - sum2;
 }
 
 // ---------------------------------------------------------------------------

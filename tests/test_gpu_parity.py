@@ -2,7 +2,11 @@
 
 Tolerances:
   * FP32 path after 1000 steps: max |rho_gpu - rho_oracle| / max |rho_oracle|
-    <= 1e-5 per component, and relative mass drift <= 1e-6 on closed domains;
+    <= 1e-5 per component, and relative mass drift <= 1e-6 on closed domains.
+    Cases whose interfaces can translate freely (a flat slab in a periodic
+    column, drainage fronts) have an undamped mode that FP32 round-off drives
+    like a random walk; there the FP32 path is held to 1e-5 over 200-300
+    steps and the FP64 path carries the long-horizon check;
   * FP64 path: 1e-12 on the same measure (only the summation order differs);
   * a few steps from a random non-equilibrium state: every population, FP64
     to 1e-13 absolute, FP32 to 2e-6 absolute (populations are O(0.1)).
@@ -134,7 +138,9 @@ def test_open_drainage_porous(lbm, storage, tol):
     g, o = _pair(lbm, solid, storage, **kw)
     g.init_densities(r1, r2)
     o.init_densities(r1, r2)
-    for chunk in (1, 1, 98, 300):  # odd and even step counts
+    # odd and even step counts; FP32 stops earlier because round-off drives the
+    # undamped translation mode of the free interfaces (see the module doc)
+    for chunk in ((1, 1, 98, 300) if storage == "fp64" else (1, 1, 98, 100)):
         g.step(chunk)
         o.step(chunk)
         _compare_rho(g, o, tol)
@@ -155,7 +161,7 @@ def test_walled_lateral_faces_and_xi_field(lbm):
     solid[:, :, -1] = 1
     solid[8:14, 3:7, 4:8] = 1
     rng = np.random.default_rng(5)
-    xi = rng.uniform(-0.4, 0.3, solid.shape)
+    xi = rng.uniform(-0.4, 0.3, solid.shape).astype(np.float32).astype(np.float64)  # the ABI takes float32
     r1, r2 = inputs.drainage_init(solid, 3)
     kw = dict(tau=(1.1, 0.62), G=3.5, xi_field=xi, periodic=(0, 1, 0), open_axis=2, rho_in1=1.05, rho_out2=1.0)
     g, o = _pair(lbm, solid, "fp64", **kw)
@@ -211,17 +217,18 @@ def test_degenerate_domains(lbm):
     g.step(7)
     o.step(7)
     _compare_rho(g, o, TOL_FP64_RHO)
-    # a quasi-1D column with a flat interface
+    # a quasi-1D column with two flat interfaces (a freely translating slab)
     solid = np.zeros((40, 1, 1), np.uint8)
     z = np.arange(40)[:, None, None]
     r1 = np.where((z > 10) & (z < 30), 1.0, 0.03) + 0 * solid
     r2 = np.where((z > 10) & (z < 30), 0.03, 1.0) + 0 * solid
-    g, o = _pair(lbm, solid, "fp32", tau=(1.0, 1.0), G=3.5)
-    g.init_densities(r1, r2)
-    o.init_densities(r1, r2)
-    g.step(1000)
-    o.step(1000)
-    _compare_rho(g, o, TOL_FP32_RHO)
+    for storage, steps, tol in (("fp64", 1000, TOL_FP64_RHO), ("fp32", 300, TOL_FP32_RHO)):
+        g, o = _pair(lbm, solid, storage, tau=(1.0, 1.0), G=3.5)
+        g.init_densities(r1, r2)
+        o.init_densities(r1, r2)
+        g.step(steps)
+        o.step(steps)
+        _compare_rho(g, o, tol)
     # no fluid at all
     g = lbm.Lattice(np.ones((4, 4, 4), np.uint8))
     g.init_densities(np.zeros((4, 4, 4)), np.zeros((4, 4, 4)))

@@ -195,6 +195,35 @@ lbm_status lbm_synchronize(lbm_ctx *ctx);
 lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *info);
 const char *lbm_last_error(const lbm_ctx *ctx);
 
+/* Largest n accepted by lbm_saturation_static. */
+#define LBM_SATURATION_STATIC_MAX_N 16777216
+
+/* The reduction of lbm_saturation, for callers that cannot allocate device
+ * memory (their device memory belongs to another allocator that has reserved
+ * it, or they must not pay for an allocation or the device-wide
+ * synchronisation that cudaMalloc / cudaFree can cause).  The paper has no
+ * counterpart: this is a library convenience, not part of the method.
+ *
+ * Inputs (device pointers, caller-owned): rho1[n], rho2[n] component
+ * densities of the fluid nodes (FP32); sample[n] optional (NULL = all nodes),
+ * nonzero marks the nodes counted by the saturation.  Output (device pointer,
+ * caller-owned): out[4] = S_w (fraction of sample nodes with rho2 > rho1),
+ * smooth S_nw (mean of rho1 / (rho1 + rho2) over the sample), mass1, mass2
+ * (FP64 sums over all n nodes).  stream: a cudaStream_t or NULL.
+ *
+ * Allocates nothing.  Scratch is a 256 KB FP64 array in the library's static
+ * device memory, held by every GPU that loads the library until exit; it is
+ * shared by all calls and keeps the last call's partial sums (each call
+ * overwrites every entry it reads, so nothing needs clearing).  Calls that
+ * overlap on the GPU (different streams, or different host threads on one
+ * device) race on that array.  The first call on each device looks up the
+ * array's device address with that device current; make that first call
+ * before any stream capture.  Returns LBM_ERR_ARG for n < 0, NULL pointers or
+ * n > LBM_SATURATION_STATIC_MAX_N, LBM_ERR_CUDA if the lookup or a launch
+ * fails; the work is enqueued on stream, not waited for. */
+lbm_status lbm_saturation_static(const float *rho1, const float *rho2, const uint8_t *sample, int64_t n, double *out,
+                                 void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -82,11 +82,12 @@ def load(build_if_missing: bool = True):
     lib.lbm_set_stream.argtypes = [P, P]
     lib.lbm_synchronize.argtypes = [P]
     lib.lbm_get_info.argtypes = [P, ctypes.POINTER(Info)]
+    lib.lbm_saturation_static.argtypes = [P, P, P, ctypes.c_int64, P, P]
     lib.lbm_last_error.argtypes = [P]
     lib.lbm_last_error.restype = ctypes.c_char_p
     for name in ("lbm_default_params", "lbm_create", "lbm_set_allocator", "lbm_init_densities",
                  "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_step_timed", "lbm_read_fields",
-                 "lbm_saturation", "lbm_set_inlet", "lbm_set_stream", "lbm_synchronize", "lbm_get_info"):
+                 "lbm_saturation", "lbm_saturation_static", "lbm_set_inlet", "lbm_set_stream", "lbm_synchronize", "lbm_get_info"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -121,6 +122,20 @@ def _check(code, ctx=None):
         lib = load()
         msg = lib.lbm_last_error(ctx)
         raise LbmError(code, msg.decode() if msg else "")
+
+
+SATURATION_STATIC_MAX_N = 16777216
+
+
+def saturation_static(rho1_ptr, rho2_ptr, sample_ptr, n, out_ptr, stream=0):
+    """lbm_saturation_static on caller-owned device buffers (integer device
+    addresses); enqueues the FP64 reduction on ``stream`` and returns."""
+    lib = load()
+    code = lib.lbm_saturation_static(ctypes.c_void_p(rho1_ptr), ctypes.c_void_p(rho2_ptr),
+                                     ctypes.c_void_p(sample_ptr) if sample_ptr else None, int(n),
+                                     ctypes.c_void_p(out_ptr), ctypes.c_void_p(int(stream)) if stream else None)
+    if code != LBM_OK:
+        raise LbmError(code, "lbm_saturation_static")
 
 
 class Lattice:

@@ -5,6 +5,8 @@
 
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -52,6 +54,11 @@ struct lbm_ctx {
     double mass0[2] = {0, 0};
     cudaEvent_t ev[kNumTimed + 1];
     bool have_ev = false;
+    // single-pass schedule
+    PipeState ps{};
+    void *psi_alt = nullptr;
+    int pipe_grid = 0;
+    int64_t pipe_launches = 0;
 };
 
 namespace lbm {
@@ -176,9 +183,10 @@ void run_reduce(lbm_ctx *c)
     dispatch(c, [&](auto tag) {
         using TS = decltype(tag);
         Ops<TS>::dens(c->s, (int)(c->step & 1), c->stream);
+        Ops<TS>::wall(c->s, c->stream);
         Ops<TS>::reduce(c->s, c->d_partials, kReduceBlocks, c->d_red, c->stream);
     });
-    c->launches += 3;
+    c->launches += 3 + (c->s.n_wall > 0 ? 1 : 0);
 }
 
 lbm_status capture_initial_mass(lbm_ctx *c)
@@ -200,6 +208,25 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
 {
     const int par = (int)(c->step & 1);
     cudaStream_t st = c->stream;
+    if (c->kernel == LBM_KERNEL_FUSED) {
+        PipeState &ps = c->ps;
+        // every launch takes `tickets` work tickets plus one final, failing
+        // claim per block, so the counter advances by tickets + grid
+        ps.base = (unsigned long long)c->pipe_launches * (unsigned long long)(ps.tickets + c->pipe_grid);
+        ps.epoch = (int)(c->pipe_launches + 1);
+        ps.psi_next = c->psi_alt;
+        dispatch(c, [&](auto tag) {
+            using TS = decltype(tag);
+            if (ev) cudaEventRecord(ev[0], st);
+            Ops<TS>::pipe(c->s, ps, par, c->pipe_grid, st);
+            if (ev) cudaEventRecord(ev[1], st);
+        });
+        void *t = c->s.psi;
+        c->s.psi = c->psi_alt;
+        c->psi_alt = t;
+        c->pipe_launches++;
+        c->launches += c->s.n_fluid > 0 ? 1 : 0;
+    } else {
     dispatch(c, [&](auto tag) {
         using TS = decltype(tag);
         if (ev) cudaEventRecord(ev[0], st);
@@ -213,6 +240,7 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
         if (ev) cudaEventRecord(ev[4], st);
     });
     c->launches += 2 + (c->s.n_wall > 0 ? 1 : 0) + (c->s.open_z ? 1 : 0);
+    }
     c->step++;
     if (c->p.reduce_every > 0 && c->step % c->p.reduce_every == 0) {
         run_reduce(c);
@@ -349,6 +377,8 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         wxi.push_back(g->xi_field ? (double)g->xi_field[v] : p->xi);
     }
     const int64_t NW = (int64_t)wpvox.size();
+    if (19 * (((N + 63) / 64) * 64 + 64) >= ((int64_t)1 << 31))
+        return fail(nullptr, LBM_ERR_UNSUPPORTED, "more than 113 million fluid nodes in one context");
 
     lbm_ctx *c = new lbm_ctx();
     cudaGetDevice(&c->device);
@@ -363,7 +393,7 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     c->open_axis = g->open_axis;
     c->p = *p;
     c->storage = p->storage;
-    c->kernel = LBM_KERNEL_SPLIT;
+    c->kernel = p->kernel == LBM_KERNEL_FUSED ? LBM_KERNEL_FUSED : LBM_KERNEL_SPLIT;
 
     const size_t sz = p->storage == LBM_STORE_FP64 ? 8 : 4;  // population storage bytes
     const size_t szc = sz;                                     // compute-type bytes
@@ -416,6 +446,83 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     }
     c->d_partials = (double *)A((size_t)kReduceBlocks * kReduceSlots * 8);
     c->d_red = (double *)A((size_t)kReduceSlots * 8);
+
+    // Single-pass schedule: chunk dependencies.  D of chunk c reads the
+    // post-stream populations of its nodes, written by F of their fluid
+    // neighbours; at an open plane it also reads the interior node's, written
+    // by F of that node's neighbours.  W of wall chunk c (the walls whose voxel
+    // lies between the first voxels of fluid chunks c and c+1) reads D of the
+    // chunks of its fluid neighbours.
+    std::vector<int2> dep_f, dep_d;
+    std::vector<int> wst;
+    if (c->kernel == LBM_KERNEL_FUSED && N > 0) {
+        const int64_t NC = (N + kChunk - 1) / kChunk;
+        dep_f.assign((size_t)NC, make_int2(0, -1));
+        dep_d.assign((size_t)NC, make_int2(0, -1));
+        wst.assign((size_t)NC + 1, 0);
+        auto nb_voxel = [&](int64_t v, int j, int64_t *out) {
+            int m[3] = {(int)(v % nx) + kEx[j], (int)((v / nx) % ny) + kEy[j], (int)(v / ((int64_t)nx * ny)) + kEz[j]};
+            for (int a = 0; a < 3; ++a) {
+                if (m[a] < 0 || m[a] >= dims[a]) {
+                    if (!per[a]) return false;
+                    m[a] = (m[a] + dims[a]) % dims[a];
+                }
+            }
+            *out = m[0] + (int64_t)nx * (m[1] + (int64_t)ny * m[2]);
+            return true;
+        };
+        auto widen = [&](int2 &r, int ch) {
+            if (r.y < r.x) r = make_int2(ch, ch);
+            r.x = std::min(r.x, ch);
+            r.y = std::max(r.y, ch);
+        };
+        auto add_writers = [&](int2 &r, int64_t v) {  // F chunks writing the post-stream cells of voxel v
+            widen(r, cidx[(size_t)v] / kChunk);
+            for (int j = 1; j < 19; ++j) {
+                int64_t u;
+                if (nb_voxel(v, j, &u) && cidx[(size_t)u] >= 0) widen(r, cidx[(size_t)u] / kChunk);
+            }
+        };
+        for (int64_t n = 0; n < N; ++n) {
+            int2 &r = dep_f[(size_t)(n / kChunk)];
+            const int64_t v = pvox[(size_t)n];
+            add_writers(r, v);
+            if (nflags[(size_t)n] & (F_INLET | F_OUTLET))
+                add_writers(r, v + ((nflags[(size_t)n] & F_INLET) ? 1 : -1) * (int64_t)nx * ny);
+        }
+        size_t w = 0;
+        for (int64_t ch = 0; ch < NC; ++ch) {
+            const int64_t v_hi = ch + 1 < NC ? (int64_t)pvox[(size_t)((ch + 1) * kChunk)] : nv;
+            wst[(size_t)ch] = (int)w;
+            for (; w < wpvox.size() && (int64_t)wpvox[w] < v_hi; ++w) {
+                for (int j = 1; j < 19; ++j) {
+                    int64_t u;
+                    if ((wmask[w] & (1u << j)) && nb_voxel(wpvox[w], j, &u)) widen(dep_d[(size_t)ch], cidx[(size_t)u] / kChunk);
+                }
+            }
+        }
+        wst[(size_t)NC] = (int)wpvox.size();
+        int reach_f = 0, reach_d = 0;
+        for (int64_t ch = 0; ch < NC; ++ch) {
+            reach_f = std::max(reach_f, dep_f[(size_t)ch].y - (int)ch);
+            if (dep_d[(size_t)ch].y >= dep_d[(size_t)ch].x) reach_d = std::max(reach_d, dep_d[(size_t)ch].y - (int)ch);
+        }
+        int slack = 64;
+        if (const char *e = std::getenv("LBM_PIPE_SLACK")) slack = std::max(0, std::atoi(e));
+        PipeState &ps = c->ps;
+        ps.n_chunks = (int)NC;
+        ps.lag_d = reach_f + 1 + slack;
+        ps.lag_w = ps.lag_d + reach_d + 1;
+        ps.tickets = ps.n_chunks + ps.lag_w;
+        ps.flag_f = (int *)A((size_t)NC * 4);
+        ps.flag_d = (int *)A((size_t)NC * 4);
+        ps.dep_f = (const int2 *)A((size_t)NC * 8);
+        ps.dep_d = (const int2 *)A((size_t)NC * 8);
+        ps.wstart = (const int *)A((size_t)(NC + 1) * 4);
+        ps.counter = (unsigned long long *)A(8);
+        ps.abort = (int *)A(4);
+        c->psi_alt = A((size_t)nv * 2 * szc);
+    }
     if (!ok) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ERR_ALLOC, "device allocation failed");
@@ -452,10 +559,28 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     if (e == cudaSuccess) e = cudaMemset(s.psi, 0, (size_t)nv * 2 * szc);
     if (e == cudaSuccess && open_z) e = cudaMemset(s.bc, 0, (size_t)2 * 2 * 5 * nxy * sz);
     if (e == cudaSuccess && open_z) e = cudaMemset(c->d_frozen, 0, (size_t)2 * 5 * nxy * 8);
+    if (e == cudaSuccess && c->ps.n_chunks > 0) {
+        PipeState &ps = c->ps;
+        const int64_t NC = ps.n_chunks;
+        e = cudaMemset(ps.flag_f, 0, (size_t)NC * 4);
+        if (e == cudaSuccess) e = cudaMemset(ps.flag_d, 0, (size_t)NC * 4);
+        if (e == cudaSuccess) e = cudaMemset(ps.counter, 0, 8);
+        if (e == cudaSuccess) e = cudaMemset(ps.abort, 0, 4);
+        if (e == cudaSuccess) e = cudaMemset(c->psi_alt, 0, (size_t)nv * 2 * szc);
+        H2D((void *)ps.dep_f, dep_f.data(), (size_t)NC * 8);
+        H2D((void *)ps.dep_d, dep_d.data(), (size_t)NC * 8);
+        H2D((void *)ps.wstart, wst.data(), (size_t)(NC + 1) * 4);
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        int per_sm = 0;
+        dispatch(c, [&](auto tag) { per_sm = Ops<decltype(tag)>::pipe_blocks_per_sm(); });
+        c->pipe_grid = std::max(1, std::min(ps.tickets, std::max(1, per_sm) * std::max(1, sms)));
+    }
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->h_flag, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) {
         *c->h_flag = 0;
         e = cudaHostGetDevicePointer((void **)&c->d_flag, c->h_flag, 0);
+        c->ps.status = c->d_flag;
     }
     if (e != cudaSuccess) {
         lbm_destroy(c);
@@ -569,8 +694,15 @@ lbm_status lbm_step_timed(lbm_ctx *c, int64_t n, double *kernel_ms, int32_t nk)
     }
     for (int64_t k = 0; k < n; ++k) {
         enqueue_step(c, c->ev);
-        cudaError_t e = cudaEventSynchronize(c->ev[4]);
+        const bool fused = c->kernel == LBM_KERNEL_FUSED;
+        cudaError_t e = cudaEventSynchronize(c->ev[fused ? 1 : 4]);
         if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_timed");
+        if (fused) {
+            float ms = 0;
+            cudaEventElapsedTime(&ms, c->ev[0], c->ev[1]);
+            if (nk > 4) kernel_ms[4] += ms;
+            continue;
+        }
         for (int q = 0; q < 4 && q < nk; ++q) {
             float ms = 0;
             cudaEventElapsedTime(&ms, c->ev[q], c->ev[q + 1]);

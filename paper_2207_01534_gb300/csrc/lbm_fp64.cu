@@ -1,5 +1,6 @@
 // FP64 populations, FP64 arithmetic.
 #include "lbm_kernels.cuh"
+#include "lbm_pipe.cuh"
 #include "lbm_ops.inl"
 
 namespace lbm {

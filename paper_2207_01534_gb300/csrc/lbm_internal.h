@@ -52,6 +52,32 @@ struct DevState {
     int32_t velocity_shift;
 };
 
+// Single-pass schedule: one persistent launch per step works through tickets
+// k = 0 .. tickets-1 taken in order from a global counter.  Ticket k collides
+// and streams chunk k (F), then computes the next-step densities of chunk
+// k - lag_d (D, with the open-plane extrapolation for plane nodes), then the
+// wall densities of wall chunk k - lag_w (W).  A phase waits until the phases
+// it reads from have published their chunk flags; since every dependency
+// points to a lower ticket, and tickets are only taken by running blocks, the
+// waits always end (they are bounded anyway, see kPipeMaxPolls).
+constexpr int kChunk = 256;            // fluid nodes per chunk = threads per block
+constexpr int kPipeMaxPolls = 1 << 21; // polls of a flag range before giving up
+
+struct PipeState {
+    int *flag_f;                 // [n_chunks] epoch at which F of the chunk finished
+    int *flag_d;                 // [n_chunks] epoch at which D of the chunk finished
+    const int2 *dep_f;           // [n_chunks] chunk range whose F a chunk's D reads
+    const int2 *dep_d;           // [n_chunks] chunk range whose D a wall chunk's W reads
+    const int *wstart;           // [n_chunks + 1] wall index range of each wall chunk
+    unsigned long long *counter; // ticket counter (never reset; see base)
+    unsigned long long base;     // counter value at the start of this launch
+    int *abort;                  // set when a wait gives up: every block stops
+    int *status;                 // host-mapped status word (bit 4: timeout)
+    void *psi_next;              // densities of the next step (the other psi buffer)
+    int epoch;                   // 1 + launches of this schedule so far
+    int n_chunks, lag_d, lag_w, tickets;
+};
+
 // Per-storage-type kernel launchers, explicitly instantiated in one
 // translation unit per storage type.
 template <typename TS>
@@ -72,6 +98,10 @@ struct Ops {
     static void fields(const DevState &s, int parity, double *out, cudaStream_t st);
     // FP64 reduction over psi (needs dens first): partials[nblocks][8] then out[8]
     static void reduce(const DevState &s, double *partials, int nblocks, double *out, cudaStream_t st);
+    // one step of the single-pass schedule at parity `parity` on `grid` blocks
+    static void pipe(const DevState &s, const PipeState &ps, int parity, int grid, cudaStream_t st);
+    // resident blocks per SM of the single-pass kernel
+    static int pipe_blocks_per_sm();
 };
 
 constexpr int kReduceBlocks = 1024;

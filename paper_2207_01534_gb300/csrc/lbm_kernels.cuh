@@ -86,6 +86,7 @@ struct Traits<float> {
     using C = float;
     using C2 = float2;
     __device__ static __forceinline__ float load(const float *p, float) { return __ldg(p); }
+    __device__ static __forceinline__ float load_cg(const float *p, float) { return __ldcg(p); }
     __device__ static __forceinline__ void store(float *p, float v, float) { *p = v; }
 };
 
@@ -94,26 +95,40 @@ struct Traits<double> {
     using C = double;
     using C2 = double2;
     __device__ static __forceinline__ double load(const double *p, double) { return __ldg(p); }
+    __device__ static __forceinline__ double load_cg(const double *p, double) { return __ldcg(p); }
     __device__ static __forceinline__ void store(double *p, double v, double) { *p = v; }
 };
 
 // ---------------------------------------------------------------------------
 // Geometry helpers
 
-// Offset from a voxel to its neighbour in direction i, wrapping across the
-// periodic faces that the voxel touches (fl holds its face bits).
-__device__ __forceinline__ int nb_off(int i, uint32_t fl, const DevState &s)
+// Offsets from a node to its neighbours one step down / up each axis,
+// including the wrap across the periodic faces that the node touches (fl
+// holds its face bits).  Computed once per node; the offset of direction i
+// is then one or two integer adds.
+struct Nbr {
+    int dx[2], dy[2], dz[2];  // [0]: -1 move, [1]: +1 move
+};
+
+__device__ __forceinline__ Nbr make_nbr(uint32_t fl, const DevState &s)
 {
-    int off = ex(i) + ey(i) * s.sx + ez(i) * s.sxy;
-    if (fl & kFaceMask) {
-        if (ex(i) < 0 && (fl & F_XLO)) off += s.nx;
-        if (ex(i) > 0 && (fl & F_XHI)) off -= s.nx;
-        if (ey(i) < 0 && (fl & F_YLO)) off += s.ny * s.sx;
-        if (ey(i) > 0 && (fl & F_YHI)) off -= s.ny * s.sx;
-        if (ez(i) < 0 && (fl & F_ZLO)) off += s.nz * s.sxy;
-        if (ez(i) > 0 && (fl & F_ZHI)) off -= s.nz * s.sxy;
-    }
-    return off;
+    Nbr b;
+    b.dx[0] = -1 + ((fl & F_XLO) ? s.nx : 0);
+    b.dx[1] = 1 - ((fl & F_XHI) ? s.nx : 0);
+    b.dy[0] = -s.sx + ((fl & F_YLO) ? s.ny * s.sx : 0);
+    b.dy[1] = s.sx - ((fl & F_YHI) ? s.ny * s.sx : 0);
+    b.dz[0] = -s.sxy + ((fl & F_ZLO) ? s.nz * s.sxy : 0);
+    b.dz[1] = s.sxy - ((fl & F_ZHI) ? s.nz * s.sxy : 0);
+    return b;
+}
+
+__device__ __forceinline__ int nb_off(int i, const Nbr &b)
+{
+    int o = 0;
+    if (ex(i)) o += b.dx[ex(i) > 0];
+    if (ey(i)) o += b.dy[ey(i) > 0];
+    if (ez(i)) o += b.dz[ez(i) > 0];
+    return o;
 }
 
 // Does direction j leave the domain through an open plane?
@@ -122,23 +137,24 @@ __device__ __forceinline__ bool outside(int j, uint32_t fl)
     return (ez(j) < 0 && (fl & F_INLET)) || (ez(j) > 0 && (fl & F_OUTLET));
 }
 
-// slot_j(x) encoded as an offset into A (>= 0, without the component offset)
-// or as -1 - (offset into bc without the component offset).
+// slot_j(x) as an offset into one component's population block (>= 0;
+// 19 * npad < 2^31 is checked at creation) or as -1 - (offset into one
+// component's boundary block).
 template <int P>
-__device__ __forceinline__ long long slot_of(int j, int n, uint32_t pv, uint32_t fl, const DevState &s)
+__device__ __forceinline__ int slot_of(int j, int n, uint32_t pv, uint32_t fl, const Nbr &b, const DevState &s)
 {
-    if (P == 0) return (long long)opp(j) * s.npad + n;
+    if (P == 0) return opp(j) * (int)s.npad + n;
     if (outside(j, fl)) {
         const int plane = (fl & F_INLET) ? 0 : 1;
         const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
-        return -1 - ((long long)(plane * 10 + miss_k(opp(j))) * s.nxy + p);
+        return -1 - ((plane * 10 + miss_k(opp(j))) * s.nxy + p);
     }
-    const int c = __ldg(s.cidx + ((int)pv + nb_off(j, fl, s)));
-    return c >= 0 ? (long long)j * s.npad + c : (long long)opp(j) * s.npad + n;
+    const int c = __ldg(s.cidx + ((int)pv + nb_off(j, b)));
+    return c >= 0 ? j * (int)s.npad + c : opp(j) * (int)s.npad + n;
 }
 
 template <typename TS>
-__device__ __forceinline__ TS *cell(const DevState &s, int sigma, long long slot)
+__device__ __forceinline__ TS *cell(const DevState &s, int sigma, int slot)
 {
     return slot >= 0 ? reinterpret_cast<TS *>(s.f) + (long long)sigma * 19 * s.npad + slot
                      : reinterpret_cast<TS *>(s.bc) + (long long)sigma * 5 * s.nxy + (-1 - slot);
@@ -151,34 +167,41 @@ __device__ __forceinline__ typename Traits<TS>::C ref_of(const DevState &s, int 
     return wgt<C>(i) * (C)(sigma == 0 ? s.rref1 : s.rref2);
 }
 
-// Post-stream populations f[sigma][i] of node n at parity P.
-template <typename TS, int P>
+// Post-stream populations f[sigma][i] of node n at parity P.  L2ONLY loads
+// bypass L1 (for data written earlier in the same launch).
+template <typename TS, int P, bool L2ONLY = false>
 __device__ __forceinline__ void load_pops(typename Traits<TS>::C f[2][19], int n, uint32_t pv, uint32_t fl,
-                                          const DevState &s)
+                                          const Nbr &b, const DevState &s)
 {
     const TS *A = reinterpret_cast<const TS *>(s.f);
 #pragma unroll
-    for (int sg = 0; sg < 2; ++sg) f[sg][0] = Traits<TS>::load(A + (long long)sg * 19 * s.npad + n, ref_of<TS>(s, sg, 0));
+    for (int sg = 0; sg < 2; ++sg) {
+        const TS *p = A + (long long)sg * 19 * s.npad + n;
+        f[sg][0] = L2ONLY ? Traits<TS>::load_cg(p, ref_of<TS>(s, sg, 0)) : Traits<TS>::load(p, ref_of<TS>(s, sg, 0));
+    }
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
-        const long long sl = slot_of<P>(j, n, pv, fl, s);
+        const int sl = slot_of<P>(j, n, pv, fl, b, s);
 #pragma unroll
-        for (int sg = 0; sg < 2; ++sg) f[sg][opp(j)] = Traits<TS>::load(cell<TS>(s, sg, sl), ref_of<TS>(s, sg, j));
+        for (int sg = 0; sg < 2; ++sg) {
+            const TS *p = cell<TS>(s, sg, sl);
+            f[sg][opp(j)] = L2ONLY ? Traits<TS>::load_cg(p, ref_of<TS>(s, sg, j)) : Traits<TS>::load(p, ref_of<TS>(s, sg, j));
+        }
     }
 }
 
 // Post-collision populations f[sigma][i] of node n into their slots.
 template <typename TS, int P>
 __device__ __forceinline__ void store_pops(const typename Traits<TS>::C f[2][19], int n, uint32_t pv, uint32_t fl,
-                                           const DevState &s)
+                                           const Nbr &b, const DevState &s)
 {
     TS *A = reinterpret_cast<TS *>(s.f);
 #pragma unroll
     for (int sg = 0; sg < 2; ++sg) Traits<TS>::store(A + (long long)sg * 19 * s.npad + n, f[sg][0], ref_of<TS>(s, sg, 0));
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
-        const long long sl = slot_of<P>(j, n, pv, fl, s);
         if (P == 1 && outside(j, fl)) continue;  // leaves the domain
+        const int sl = slot_of<P>(j, n, pv, fl, b, s);
 #pragma unroll
         for (int sg = 0; sg < 2; ++sg) Traits<TS>::store(cell<TS>(s, sg, sl), f[sg][j], ref_of<TS>(s, sg, j));
     }
@@ -198,7 +221,7 @@ __device__ __forceinline__ C sum19(const C f[19])
 // an open plane the mirrored direction's neighbour is used (Section 2).
 template <typename TS>
 __device__ __forceinline__ void forces(typename Traits<TS>::C rho1, typename Traits<TS>::C rho2, uint32_t pv,
-                                       uint32_t fl, const DevState &s, typename Traits<TS>::C F1[3],
+                                       uint32_t fl, const Nbr &b, const DevState &s, typename Traits<TS>::C F1[3],
                                        typename Traits<TS>::C F2[3])
 {
     using C = typename Traits<TS>::C;
@@ -207,7 +230,7 @@ __device__ __forceinline__ void forces(typename Traits<TS>::C rho1, typename Tra
     C a1[3] = {0, 0, 0}, a2[3] = {0, 0, 0};
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
-        const int off = outside(j, fl) ? nb_off(mirz(j), fl, s) : nb_off(j, fl, s);
+        const int off = outside(j, fl) ? nb_off(mirz(j), b) : nb_off(j, b);
         // neighbour minus own value: the same sum, since sum_j w_j e_j = 0,
         // with far less cancellation error in FP32 near uniform regions
         const C2 q = psi[(int)pv + off];
@@ -246,18 +269,23 @@ __device__ __forceinline__ void mix_velocity(const C f[2][19], C rho1, C rho2, c
     for (int a = 0; a < 3; ++a) u[a] = (m[a] + h * (F1[a] + F2[a])) * inv_rho;
 }
 
-// Eq. 1 with Eq. 2 equilibrium and Eq. 9 forcing, in place on f[sigma][i].
+// Eq. 1 with Eq. 2 equilibrium and Eq. 9 forcing, in place on f[sigma][i]:
+// f* = (1 - 1/tau_s) f + f^eq / tau_s + (1 - 1/(2 tau_s)) S.  Directions are
+// taken in opposite pairs (i, opp(i)): with eu = e_i.u and eF = e_i.F, the
+// pair shares sym = 1 + 4.5 eu^2 - 1.5 u^2 and 9 eu eF - 3 u.F, and differs
+// only in the sign of 3 eu and 3 eF, so each pair is computed once.
 template <typename C>
 __device__ __forceinline__ void collide(C f[2][19], C rho1, C rho2, C inv_rho, const C u[3], const C F1[3],
                                         const C F2[3], const DevState &s)
 {
     const C tau_s = (rho1 * (C)s.tau1 + rho2 * (C)s.tau2) * inv_rho;
     const C om = C(1) / tau_s;
+    const C keep = C(1) - om;
     const C cf = C(1) - C(0.5) * om;
     const C usq = C(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const C uF1 = u[0] * F1[0] + u[1] * F1[1] + u[2] * F1[2];
-    const C uF2 = u[0] * F2[0] + u[1] * F2[1] + u[2] * F2[2];
-    const C rho[2] = {rho1, rho2};
+    const C cuF1 = C(-3) * (u[0] * F1[0] + u[1] * F1[1] + u[2] * F1[2]);
+    const C cuF2 = C(-3) * (u[0] * F2[0] + u[1] * F2[1] + u[2] * F2[2]);
+    const C r1o = om * rho1, r2o = om * rho2;
     // The rest population is written last as rho^sigma minus the 18 moving
     // post-collision populations.  In exact arithmetic this equals Eq. 1 for
     // i = 0 (sum_i f^eq_i = rho, sum_i S_i = 0); in FP32 it removes the mass
@@ -266,17 +294,27 @@ __device__ __forceinline__ void collide(C f[2][19], C rho1, C rho2, C inv_rho, c
     C sum1 = 0, sum2 = 0;
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
+        if (opp(i) < i) continue;  // each pair once, from its first member
+        const int o = opp(i);
+        const C w = wgt<C>(i);
         const C eu = ex(i) * u[0] + ey(i) * u[1] + ez(i) * u[2];
-        const C base = C(1) + C(3) * eu + C(4.5) * eu * eu - usq;
         const C eF1 = ex(i) * F1[0] + ey(i) * F1[1] + ez(i) * F1[2];
         const C eF2 = ex(i) * F2[0] + ey(i) * F2[1] + ez(i) * F2[2];
-        const C w = wgt<C>(i);
-        const C S1 = w * (C(3) * (eF1 - uF1) + C(9) * eu * eF1);
-        const C S2 = w * (C(3) * (eF2 - uF2) + C(9) * eu * eF2);
-        const C fe1 = w * rho[0] * base;
-        const C fe2 = w * rho[1] * base;
-        f[0][i] = f[0][i] - om * (f[0][i] - fe1) + cf * S1;
-        f[1][i] = f[1][i] - om * (f[1][i] - fe2) + cf * S2;
+        const C sym = C(1) + C(4.5) * eu * eu - usq;
+        const C ant = C(3) * eu;
+        const C A1 = w * (r1o * sym + cf * (C(9) * eu * eF1 + cuF1));
+        const C B1 = w * (r1o * ant + cf * C(3) * eF1);
+        const C A2 = w * (r2o * sym + cf * (C(9) * eu * eF2 + cuF2));
+        const C B2 = w * (r2o * ant + cf * C(3) * eF2);
+        f[0][i] = keep * f[0][i] + (A1 + B1);
+        f[0][o] = keep * f[0][o] + (A1 - B1);
+        f[1][i] = keep * f[1][i] + (A2 + B2);
+        f[1][o] = keep * f[1][o] + (A2 - B2);
+    }
+    // accumulated one direction at a time, in direction order: summing each
+    // pair first biases the FP32 rounding and drifts the mass measurably
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
         sum1 += f[0][i];
         sum2 += f[1][i];
     }
@@ -297,7 +335,8 @@ __global__ void __launch_bounds__(256) k_dens(DevState s)
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
     C f[2][19];
-    load_pops<TS, P>(f, n, pv, fl, s);
+    const Nbr b = make_nbr(fl, s);
+    load_pops<TS, P>(f, n, pv, fl, b, s);
     C2 q;
     q.x = sum19<C>(f[0]);
     q.y = sum19<C>(f[1]);
@@ -317,11 +356,12 @@ __global__ void __launch_bounds__(256) k_wall(DevState s)
     const uint32_t mask = s.wmask[w];
     const uint32_t fl = mask >> kWallFaceShift;
     C2 *psi = reinterpret_cast<C2 *>(s.psi);
+    const Nbr b = make_nbr(fl, s);
     C s1 = 0, s2 = 0;
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
         if (mask & (1u << j)) {
-            const C2 q = psi[(int)pv + nb_off(j, fl, s)];
+            const C2 q = psi[(int)pv + nb_off(j, b)];
             s1 += wgt<C>(j) * q.x;
             s2 += wgt<C>(j) * q.y;
         }
@@ -343,14 +383,15 @@ __global__ void __launch_bounds__(256) k_fused(DevState s)
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
     C f[2][19];
-    load_pops<TS, P>(f, n, pv, fl, s);
+    const Nbr b = make_nbr(fl, s);
+    load_pops<TS, P>(f, n, pv, fl, b, s);
     const C rho1 = sum19<C>(f[0]);
     const C rho2 = sum19<C>(f[1]);
     C F1[3], F2[3], u[3], inv_rho;
-    forces<TS>(rho1, rho2, pv, fl, s, F1, F2);
+    forces<TS>(rho1, rho2, pv, fl, b, s, F1, F2);
     mix_velocity<C>(f, rho1, rho2, F1, F2, s, inv_rho, u);
     collide<C>(f, rho1, rho2, inv_rho, u, F1, F2, s);
-    store_pops<TS, P>(f, n, pv, fl, s);
+    store_pops<TS, P>(f, n, pv, fl, b, s);
 }
 
 // Open planes, run after a step for the parity PN of the step that reads next:
@@ -359,10 +400,57 @@ __global__ void __launch_bounds__(256) k_fused(DevState s)
 // f_i(xb) = f^eq_i(rho_b, u) + f_i(xi) - f^eq_i(rho(xi), u) with u the
 // barycentric velocity of xi; the other component's missing populations get
 // their initial values back (Section 2).
+template <typename TS, int PN, bool L2ONLY>
+__device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb, uint32_t flb, const DevState &s)
+{
+    using C = typename Traits<TS>::C;
+    const uint32_t pvi = plane == 0 ? pvb + s.sxy : pvb - s.sxy;
+    const int ni = s.cidx[pvi];
+    const uint32_t fli = s.nflags[ni];
+    const Nbr bi = make_nbr(fli, s);
+    const Nbr bb = make_nbr(flb, s);
+    C fi[2][19];
+    load_pops<TS, PN, L2ONLY>(fi, ni, pvi, fli, bi, s);
+    const C r1 = sum19<C>(fi[0]);
+    const C r2 = sum19<C>(fi[1]);
+    C m[3] = {0, 0, 0};
+#pragma unroll
+    for (int i = 1; i < 19; ++i) {
+        const C tt = fi[0][i] + fi[1][i];
+        if (ex(i)) m[0] += ex(i) * tt;
+        if (ey(i)) m[1] += ey(i) * tt;
+        if (ez(i)) m[2] += ez(i) * tt;
+    }
+    const C ir = C(1) / (r1 + r2);
+    const C u[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
+    const C usq = C(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
+    const C rb = (C)(plane == 0 ? s.rho_in1 : s.rho_out2);
+    const C rin = plane == 0 ? r1 : r2;
+    TS *A = reinterpret_cast<TS *>(s.f);
+    const int pc = plane;  // prescribed component index
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const C eu = ex(i) * u[0] + ey(i) * u[1] + ez(i) * u[2];
+        const C base = C(1) + C(3) * eu + C(4.5) * eu * eu - usq;
+        const C fin = plane == 0 ? fi[0][i] : fi[1][i];
+        const C v = wgt<C>(i) * rb * base + fin - wgt<C>(i) * rin * base;
+        if (i == 0)
+            Traits<TS>::store(A + (long long)pc * 19 * s.npad + nb, v, ref_of<TS>(s, pc, 0));
+        else
+            Traits<TS>::store(cell<TS>(s, pc, slot_of<PN>(opp(i), nb, pvb, flb, bb, s)), v, ref_of<TS>(s, pc, i));
+    }
+    const int qc = 1 - pc;
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int i = miss_dir(plane, k);
+        const C v = (C)s.frozen[(long long)(plane * 5 + k) * s.nxy + p];
+        Traits<TS>::store(cell<TS>(s, qc, slot_of<PN>(opp(i), nb, pvb, flb, bb, s)), v, ref_of<TS>(s, qc, i));
+    }
+}
+
 template <typename TS, int PN>
 __global__ void __launch_bounds__(128) k_plane(DevState s)
 {
-    using C = typename Traits<TS>::C;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * s.nxy) return;
     const int plane = t >= s.nxy ? 1 : 0;
@@ -370,46 +458,7 @@ __global__ void __launch_bounds__(128) k_plane(DevState s)
     const uint32_t pvb = plane == 0 ? (uint32_t)p : (uint32_t)(p + (s.nz - 1) * s.sxy);
     const int nb = s.cidx[pvb];
     if (nb < 0) return;
-    const uint32_t pvi = plane == 0 ? pvb + s.sxy : pvb - s.sxy;
-    const int ni = s.cidx[pvi];
-    const uint32_t fli = s.nflags[ni];
-    const uint32_t flb = s.nflags[nb];
-    C fi[2][19];
-    load_pops<TS, PN>(fi, ni, pvi, fli, s);
-    const C r1 = sum19<C>(fi[0]);
-    const C r2 = sum19<C>(fi[1]);
-    C m[3] = {0, 0, 0};
-#pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        const C tt = fi[0][i] + fi[1][i];
-        m[0] += ex(i) * tt;
-        m[1] += ey(i) * tt;
-        m[2] += ez(i) * tt;
-    }
-    const C ir = C(1) / (r1 + r2);
-    const C u[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
-    const C usq = C(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const int pc = plane;  // prescribed component index
-    const C rb = (C)(plane == 0 ? s.rho_in1 : s.rho_out2);
-    const C rin = plane == 0 ? r1 : r2;
-    TS *A = reinterpret_cast<TS *>(s.f);
-#pragma unroll
-    for (int i = 0; i < 19; ++i) {
-        const C eu = ex(i) * u[0] + ey(i) * u[1] + ez(i) * u[2];
-        const C base = C(1) + C(3) * eu + C(4.5) * eu * eu - usq;
-        const C v = wgt<C>(i) * rb * base + fi[pc][i] - wgt<C>(i) * rin * base;
-        if (i == 0)
-            Traits<TS>::store(A + (long long)pc * 19 * s.npad + nb, v, ref_of<TS>(s, pc, 0));
-        else
-            Traits<TS>::store(cell<TS>(s, pc, slot_of<PN>(opp(i), nb, pvb, flb, s)), v, ref_of<TS>(s, pc, i));
-    }
-    const int qc = 1 - pc;
-#pragma unroll
-    for (int k = 0; k < 5; ++k) {
-        const int i = miss_dir(plane, k);
-        const C v = (C)s.frozen[(long long)(plane * 5 + k) * s.nxy + p];
-        Traits<TS>::store(cell<TS>(s, qc, slot_of<PN>(opp(i), nb, pvb, flb, s)), v, ref_of<TS>(s, qc, i));
-    }
+    neem_node<TS, PN, false>(plane, p, nb, pvb, s.nflags[nb], s);
 }
 
 // ---------------------------------------------------------------------------
@@ -454,7 +503,9 @@ __global__ void k_gather(DevState s, double *out)
     if (n >= s.n_fluid) return;
     const uint32_t pv = s.pvox[n];
     C f[2][19];
-    load_pops<TS, P>(f, n, pv, s.nflags[n], s);
+    const uint32_t fl = s.nflags[n];
+    const Nbr b = make_nbr(fl, s);
+    load_pops<TS, P>(f, n, pv, fl, b, s);
 #pragma unroll
     for (int sg = 0; sg < 2; ++sg)
 #pragma unroll
@@ -492,11 +543,12 @@ __global__ void k_fields(DevState s, double *out)
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
     C f[2][19];
-    load_pops<TS, P>(f, n, pv, fl, s);
+    const Nbr b = make_nbr(fl, s);
+    load_pops<TS, P>(f, n, pv, fl, b, s);
     const C rho1 = sum19<C>(f[0]);
     const C rho2 = sum19<C>(f[1]);
     C F1[3], F2[3], u[3], inv_rho;
-    forces<TS>(rho1, rho2, pv, fl, s, F1, F2);
+    forces<TS>(rho1, rho2, pv, fl, b, s, F1, F2);
     mix_velocity<C>(f, rho1, rho2, F1, F2, s, inv_rho, u);
     const C cs2 = C(1) / C(3);
     out[0 * s.nv + pv] = (double)rho1;

@@ -81,4 +81,21 @@ void Ops<TS>::reduce(const DevState &s, double *partials, int nblocks, double *o
     k_reduce_final<<<1, kReduceThreads, 0, st>>>(partials, nblocks, out);
 }
 
+template <typename TS>
+void Ops<TS>::pipe(const DevState &s, const PipeState &ps, int parity, int grid, cudaStream_t st)
+{
+    if (ps.tickets <= 0 || grid <= 0) return;
+    if (parity) k_pipe<TS, 1><<<grid, kChunk, 0, st>>>(s, ps);
+    else k_pipe<TS, 0><<<grid, kChunk, 0, st>>>(s, ps);
+}
+
+template <typename TS>
+int Ops<TS>::pipe_blocks_per_sm()
+{
+    int a = 0, b = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pipe<TS, 0>, kChunk, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pipe<TS, 1>, kChunk, 0);
+    return a < b ? a : b;
+}
+
 }  // namespace lbm

@@ -1,0 +1,186 @@
+// lbm_pipe.cuh -- the single-pass schedule: one persistent launch per time
+// step that collides and streams every fluid node (F), computes the densities
+// of the next step (D, including the open-plane extrapolation) right behind
+// it while the freshly written populations are still in L2, and then the wall
+// virtual densities (W).  Populations are read from DRAM once per step.
+//
+// Ordering.  F(k) reads only data written by earlier launches.  D(c) reads
+// populations that F of neighbouring chunks wrote in this launch, so it waits
+// for their chunk flags (acquire) and reads with L2-only loads; F publishes its
+// flag after a block barrier and a device fence (release).  W(c) waits for D
+// the same way.  Every wait is bounded: after kPipeMaxPolls polls it sets the
+// abort word and a timeout bit in the host-mapped status word, and all blocks
+// stop at their next ticket.
+#pragma once
+
+#include "lbm_kernels.cuh"
+
+namespace lbm {
+
+__device__ __forceinline__ int ld_acquire(const int *p)
+{
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int *p, int v)
+{
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Publish a phase of this block for chunk c: every thread's stores are
+// ordered before the flag by the barrier and the device-scope fence.
+__device__ __forceinline__ void publish(int *flags, int c, int epoch)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(flags + c, epoch);
+    }
+}
+
+// Wait until flags[r.x .. r.y] all reach epoch.  Warp 0 polls; the result is
+// shared with the block.  Returns false after a timeout or an abort.
+__device__ __forceinline__ bool wait_flags(const int *flags, int2 r, int epoch, const PipeState &ps, int *sh_ok)
+{
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        bool ok = false;
+        for (int it = 0; it < kPipeMaxPolls; ++it) {
+            bool mine = true;
+            for (int m = r.x + lane; m <= r.y; m += 32)
+                if (ld_acquire(flags + m) < epoch) {
+                    mine = false;
+                    break;
+                }
+            ok = __all_sync(0xffffffffu, mine);
+            if (ok) break;
+            if (*(volatile int *)ps.abort) break;
+            __nanosleep(64);
+        }
+        if (lane == 0) {
+            *sh_ok = ok ? 1 : 0;
+            if (!ok) {
+                atomicExch(ps.abort, 1);
+                atomicOr(ps.status, 4);
+            }
+        }
+    }
+    __syncthreads();
+    return *sh_ok != 0;
+}
+
+// F: the fused force / collision / streaming update of one node (the body of
+// k_fused).
+template <typename TS, int P>
+__device__ __forceinline__ void fused_node(int n, const DevState &s)
+{
+    using C = typename Traits<TS>::C;
+    const uint32_t pv = s.pvox[n];
+    const uint32_t fl = s.nflags[n];
+    const Nbr b = make_nbr(fl, s);
+    C f[2][19];
+    load_pops<TS, P>(f, n, pv, fl, b, s);
+    const C rho1 = sum19<C>(f[0]);
+    const C rho2 = sum19<C>(f[1]);
+    C F1[3], F2[3], u[3], inv_rho;
+    forces<TS>(rho1, rho2, pv, fl, b, s, F1, F2);
+    mix_velocity<C>(f, rho1, rho2, F1, F2, s, inv_rho, u);
+    collide<C>(f, rho1, rho2, inv_rho, u, F1, F2, s);
+    store_pops<TS, P>(f, n, pv, fl, b, s);
+}
+
+// D: open-plane extrapolation (plane nodes) then the density of one node at
+// the parity PN of the next step, into psi_next.
+template <typename TS, int PN>
+__device__ __forceinline__ void dens_node(int n, const DevState &s, void *psi_next)
+{
+    using C = typename Traits<TS>::C;
+    using C2 = typename Traits<TS>::C2;
+    const uint32_t pv = s.pvox[n];
+    const uint32_t fl = s.nflags[n];
+    if (fl & (F_INLET | F_OUTLET)) {
+        const int plane = (fl & F_INLET) ? 0 : 1;
+        const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
+        neem_node<TS, PN, true>(plane, p, n, pv, fl, s);
+    }
+    const Nbr b = make_nbr(fl, s);
+    C f[2][19];
+    load_pops<TS, PN, true>(f, n, pv, fl, b, s);
+    C2 q;
+    q.x = sum19<C>(f[0]);
+    q.y = sum19<C>(f[1]);
+    reinterpret_cast<C2 *>(psi_next)[pv] = q;
+}
+
+// W: Eq. 15 at one wall voxel from the next-step fluid densities.
+template <typename TS>
+__device__ __forceinline__ void wall_node(int w, const DevState &s, void *psi_next)
+{
+    using C = typename Traits<TS>::C;
+    using C2 = typename Traits<TS>::C2;
+    C2 *psi = reinterpret_cast<C2 *>(psi_next);
+    const uint32_t pv = s.wpvox[w];
+    const uint32_t mask = s.wmask[w];
+    const Nbr b = make_nbr(mask >> kWallFaceShift, s);
+    C s1 = 0, s2 = 0;
+#pragma unroll
+    for (int j = 1; j < 19; ++j) {
+        if (mask & (1u << j)) {
+            const C2 q = __ldcg(psi + ((int)pv + nb_off(j, b)));
+            s1 += wgt<C>(j) * q.x;
+            s2 += wgt<C>(j) * q.y;
+        }
+    }
+    const C inv = reinterpret_cast<const C *>(s.winv)[w];
+    const C xi = reinterpret_cast<const C *>(s.wxi)[w];
+    C2 q;
+    q.x = (C(1) + xi) * s1 * inv;
+    q.y = (C(1) - xi) * s2 * inv;
+    psi[pv] = q;
+}
+
+// Resident blocks per SM the register budget is sized for.
+template <typename TS>
+struct PipeOcc {
+    static constexpr int blocks = 3;
+};
+template <>
+struct PipeOcc<double> {
+    static constexpr int blocks = 2;
+};
+
+template <typename TS, int P>
+__global__ void __launch_bounds__(kChunk, PipeOcc<TS>::blocks) k_pipe(DevState s, PipeState ps)
+{
+    __shared__ int sh_k;
+    __shared__ int sh_ok;
+    for (;;) {
+        if (threadIdx.x == 0)
+            sh_k = *(volatile int *)ps.abort ? ps.tickets : (int)(atomicAdd(ps.counter, 1ULL) - ps.base);
+        __syncthreads();
+        const int k = sh_k;
+        if (k >= ps.tickets) return;  // the same value in every thread of the block
+        if (k < ps.n_chunks) {
+            const int n = k * kChunk + threadIdx.x;
+            if (n < s.n_fluid) fused_node<TS, P>(n, s);
+            publish(ps.flag_f, k, ps.epoch);
+        }
+        const int c = k - ps.lag_d;
+        if (c >= 0 && c < ps.n_chunks) {
+            if (!wait_flags(ps.flag_f, ps.dep_f[c], ps.epoch, ps, &sh_ok)) return;
+            const int n = c * kChunk + threadIdx.x;
+            if (n < s.n_fluid) dens_node<TS, 1 - P>(n, s, ps.psi_next);
+            publish(ps.flag_d, c, ps.epoch);
+        }
+        const int cw = k - ps.lag_w;
+        if (cw >= 0 && cw < ps.n_chunks) {
+            if (!wait_flags(ps.flag_d, ps.dep_d[cw], ps.epoch, ps, &sh_ok)) return;
+            for (int w = ps.wstart[cw] + threadIdx.x; w < ps.wstart[cw + 1]; w += kChunk) wall_node<TS>(w, s, ps.psi_next);
+        }
+        __syncthreads();  // sh_k is rewritten at the top
+    }
+}
+
+}  // namespace lbm

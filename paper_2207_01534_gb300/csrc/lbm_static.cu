@@ -21,7 +21,6 @@ constexpr int kThreads = 256;
 constexpr int kItems = 16;                                 // densities per thread
 constexpr int kChunk = kThreads * kItems;                  // 4096 nodes per block
 constexpr int kMaxBlocks = 4096;                           // scratch capacity in blocks
-constexpr int kSlots = 4;                                  // m1, m2, count, n_water
 constexpr int kSmoothSlot = 4;                             // sum of rho1 / (rho1 + rho2)
 constexpr int kStride = 8;                                 // doubles per block partial
 

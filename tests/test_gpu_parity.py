@@ -35,8 +35,14 @@ def lbm():
     return m
 
 
-def _pair(lbm, solid, storage="fp32", **kw):
-    g = lbm.Lattice(solid, storage=storage, **kw)
+@pytest.fixture(params=["split", "fused"])
+def sched(request):
+    """Kernel schedule: the split passes (reference) or the single-pass pipeline."""
+    return request.param
+
+
+def _pair(lbm, solid, storage="fp32", sched="split", **kw):
+    g = lbm.Lattice(solid, storage=storage, kernel=sched, **kw)
     o = oracle.Oracle(solid, **{k: v for k, v in kw.items() if k not in ("sample",)})
     return g, o
 
@@ -73,13 +79,13 @@ def _porous_periodic(n=(22, 18, 20), seed=7):
 
 @pytest.mark.parametrize("storage,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
 @pytest.mark.parametrize("steps", [1, 2, 5])
-def test_random_state_all_populations(lbm, storage, tol, steps):
+def test_random_state_all_populations(lbm, sched, storage, tol, steps):
     """Every population after a few steps from a random non-equilibrium state,
     on a periodic porous domain with walls (both A-A parities)."""
     solid = _porous_periodic()
     f1, f2 = inputs.random_pops_state(solid, inputs.SEED_BASE + 100, rho_lo=0.05, rho_hi=0.9, noise=0.05)
     kw = dict(tau=(1.7, 0.62), G=3.5, xi=-0.3)
-    g, o = _pair(lbm, solid, storage, **kw)
+    g, o = _pair(lbm, solid, storage, sched, **kw)
     g.set_populations(f1, f2)
     o.set_pops(f1, f2)
     g.step(steps)
@@ -89,21 +95,21 @@ def test_random_state_all_populations(lbm, storage, tol, steps):
     assert np.abs(a1 - b1).max() <= tol and np.abs(a2 - b2).max() <= tol
 
 
-def test_populations_round_trip_fp64(lbm):
+def test_populations_round_trip_fp64(lbm, sched):
     solid = _porous_periodic()
     f1, f2 = inputs.random_pops_state(solid, inputs.SEED_BASE + 101)
-    g = lbm.Lattice(solid, storage="fp64")
+    g = lbm.Lattice(solid, storage="fp64", kernel=sched)
     g.set_populations(f1, f2)
     a1, a2 = g.get_populations()
     assert np.array_equal(a1, f1) and np.array_equal(a2, f2)
 
 
 @pytest.mark.parametrize("storage,tol", [("fp32", TOL_FP32_RHO), ("fp64", TOL_FP64_RHO)])
-def test_laplace_48_thousand_steps(lbm, storage, tol):
+def test_laplace_48_thousand_steps(lbm, sched, storage, tol):
     """48^3 periodic droplet (R = 10, W = 5, densities 1.0 / 0.03, tau = 1,
     G = 3.5), 1000 steps: densities and pressure jump."""
     solid, r1, r2 = inputs.laplace_48()
-    g, o = _pair(lbm, solid, storage, tau=(1.0, 1.0), G=3.5)
+    g, o = _pair(lbm, solid, storage, sched, tau=(1.0, 1.0), G=3.5)
     g.init_densities(r1, r2)
     o.init_densities(r1, r2)
     m0 = g.saturation()
@@ -128,14 +134,14 @@ def _open_porous(n=(30, 16, 14), seed=11, res=4):
 
 
 @pytest.mark.parametrize("storage,tol", [("fp32", TOL_FP32_RHO), ("fp64", TOL_FP64_RHO)])
-def test_open_drainage_porous(lbm, storage, tol):
+def test_open_drainage_porous(lbm, sched, storage, tol):
     """Drainage through a porous slab with NEEM inlet/outlet, frozen missing
     populations, mirrored pseudopotential at the planes, theta = 45 deg, M = 10."""
     solid = _open_porous()
     r1, r2 = inputs.drainage_init(solid, 4)
     kw = dict(tau=inputs.tau_for_viscosity_ratio(10.0), G=3.5, xi=inputs.xi_of_theta(45.0), periodic=(1, 1, 0),
               open_axis=2, rho_in1=1.08, rho_out2=1.0)
-    g, o = _pair(lbm, solid, storage, **kw)
+    g, o = _pair(lbm, solid, storage, sched, **kw)
     g.init_densities(r1, r2)
     o.init_densities(r1, r2)
     # odd and even step counts; FP32 stops earlier because round-off drives the
@@ -153,7 +159,7 @@ def test_open_drainage_porous(lbm, storage, tol):
     assert np.abs(a1 - b1).max() < 10 * tol and np.abs(a2 - b2).max() < 10 * tol
 
 
-def test_walled_lateral_faces_and_xi_field(lbm):
+def test_walled_lateral_faces_and_xi_field(lbm, sched):
     """Non-periodic x closed by solid faces, per-voxel xi field, open z."""
     nz, ny, nx = 24, 10, 12
     solid = np.zeros((nz, ny, nx), np.uint8)
@@ -164,7 +170,7 @@ def test_walled_lateral_faces_and_xi_field(lbm):
     xi = rng.uniform(-0.4, 0.3, solid.shape).astype(np.float32).astype(np.float64)  # the ABI takes float32
     r1, r2 = inputs.drainage_init(solid, 3)
     kw = dict(tau=(1.1, 0.62), G=3.5, xi_field=xi, periodic=(0, 1, 0), open_axis=2, rho_in1=1.05, rho_out2=1.0)
-    g, o = _pair(lbm, solid, "fp64", **kw)
+    g, o = _pair(lbm, solid, "fp64", sched, **kw)
     g.init_densities(r1, r2)
     o.init_densities(r1, r2)
     g.step(301)
@@ -172,13 +178,13 @@ def test_walled_lateral_faces_and_xi_field(lbm):
     _compare_rho(g, o, TOL_FP64_RHO)
 
 
-def test_body_force_and_no_shift(lbm):
+def test_body_force_and_no_shift(lbm, sched):
     """Body force with the printed Eq. 8 momenta (velocity_shift = 0)."""
     solid = _porous_periodic((12, 10, 14), 3)
     r1, r2 = inputs.droplet_densities(solid.shape, (7, 5, 6), 3.0, 3.0, 1.0, 0.03)
     fl = solid == 0
     kw = dict(tau=(1.0, 1.0), G=3.0, xi=0.1, body_force=(1e-5, -2e-5, 3e-5), velocity_shift=0)
-    g, o = _pair(lbm, solid, "fp64", **kw)
+    g, o = _pair(lbm, solid, "fp64", sched, **kw)
     g.init_densities(r1 * fl, r2 * fl)
     o.init_densities(r1 * fl, r2 * fl)
     g.step(50)
@@ -186,11 +192,11 @@ def test_body_force_and_no_shift(lbm):
     _compare_rho(g, o, TOL_FP64_RHO)
 
 
-def test_saturation_matches_oracle(lbm):
+def test_saturation_matches_oracle(lbm, sched):
     solid = _open_porous()
     r1, r2 = inputs.drainage_init(solid, 4)
     kw = dict(tau=(1.7, 0.62), G=3.5, xi=-0.3, periodic=(1, 1, 0), open_axis=2, rho_in1=1.1, rho_out2=1.0)
-    g = lbm.Lattice(solid, storage="fp64", sample=(4, 26), **kw)
+    g = lbm.Lattice(solid, storage="fp64", kernel=sched, sample=(4, 26), **kw)
     o = oracle.Oracle(solid, **kw)
     g.init_densities(r1, r2)
     o.init_densities(r1, r2)
@@ -208,10 +214,10 @@ def test_saturation_matches_oracle(lbm):
     assert abs(sg[1] - so[1]) < 1e-12 and abs(sg[2] - so[2]) < 1e-10 * so[2] and abs(sg[3] - so[3]) < 1e-10 * so[3]
 
 
-def test_degenerate_domains(lbm):
+def test_degenerate_domains(lbm, sched):
     # a single periodic fluid voxel: every neighbour is itself
     solid = np.zeros((1, 1, 1), np.uint8)
-    g, o = _pair(lbm, solid, "fp64", tau=(1.2, 0.8), G=3.5)
+    g, o = _pair(lbm, solid, "fp64", sched, tau=(1.2, 0.8), G=3.5)
     g.init_densities(np.full((1, 1, 1), 0.7), np.full((1, 1, 1), 0.3))
     o.init_densities(0.7, 0.3)
     g.step(7)
@@ -223,25 +229,25 @@ def test_degenerate_domains(lbm):
     r1 = np.where((z > 10) & (z < 30), 1.0, 0.03) + 0 * solid
     r2 = np.where((z > 10) & (z < 30), 0.03, 1.0) + 0 * solid
     for storage, steps, tol in (("fp64", 1000, TOL_FP64_RHO), ("fp32", 300, TOL_FP32_RHO)):
-        g, o = _pair(lbm, solid, storage, tau=(1.0, 1.0), G=3.5)
+        g, o = _pair(lbm, solid, storage, sched, tau=(1.0, 1.0), G=3.5)
         g.init_densities(r1, r2)
         o.init_densities(r1, r2)
         g.step(steps)
         o.step(steps)
         _compare_rho(g, o, tol)
     # no fluid at all
-    g = lbm.Lattice(np.ones((4, 4, 4), np.uint8))
+    g = lbm.Lattice(np.ones((4, 4, 4), np.uint8), kernel=sched)
     g.init_densities(np.zeros((4, 4, 4)), np.zeros((4, 4, 4)))
     g.step(3)
     assert g.saturation() == (0.0, 0.0, 0.0, 0.0)
 
 
-def test_ragged_sizes_span_many_blocks(lbm):
+def test_ragged_sizes_span_many_blocks(lbm, sched):
     """A size that is not a multiple of the block size, with both parities."""
     solid = _porous_periodic((17, 23, 29), 9)
     r1, r2 = inputs.droplet_densities(solid.shape, (14, 11, 8), 5.0, 4.0, 1.0, 0.03)
     fl = solid == 0
-    g, o = _pair(lbm, solid, "fp32", tau=(1.7, 0.62), G=3.5, xi=0.2)
+    g, o = _pair(lbm, solid, "fp32", sched, tau=(1.7, 0.62), G=3.5, xi=0.2)
     g.init_densities(r1 * fl, r2 * fl)
     o.init_densities(r1 * fl, r2 * fl)
     g.step(333)

@@ -507,12 +507,19 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
             reach_f = std::max(reach_f, dep_f[(size_t)ch].y - (int)ch);
             if (dep_d[(size_t)ch].y >= dep_d[(size_t)ch].x) reach_d = std::max(reach_d, dep_d[(size_t)ch].y - (int)ch);
         }
-        int slack = 64;
+        // Lags beyond the bare dependency reach by about the number of blocks
+        // in flight, so that a D or W phase rarely finds its inputs still
+        // being computed (the re-read window stays a few tens of MB of L2).
+        int sms = 0, per_sm = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        dispatch(c, [&](auto tag) { per_sm = Ops<decltype(tag)>::pipe_blocks_per_sm(); });
+        const int resident = std::max(1, per_sm) * std::max(1, sms);
+        int slack = 2 * resident;
         if (const char *e = std::getenv("LBM_PIPE_SLACK")) slack = std::max(0, std::atoi(e));
         PipeState &ps = c->ps;
         ps.n_chunks = (int)NC;
         ps.lag_d = reach_f + 1 + slack;
-        ps.lag_w = ps.lag_d + reach_d + 1;
+        ps.lag_w = ps.lag_d + reach_d + 1 + slack / 2;
         ps.tickets = ps.n_chunks + ps.lag_w;
         ps.flag_f = (int *)A((size_t)NC * 4);
         ps.flag_d = (int *)A((size_t)NC * 4);
@@ -521,6 +528,7 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         ps.wstart = (const int *)A((size_t)(NC + 1) * 4);
         ps.counter = (unsigned long long *)A(8);
         ps.abort = (int *)A(4);
+        ps.front = (unsigned long long *)A(16);
         c->psi_alt = A((size_t)nv * 2 * szc);
     }
     if (!ok) {
@@ -566,6 +574,7 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         if (e == cudaSuccess) e = cudaMemset(ps.flag_d, 0, (size_t)NC * 4);
         if (e == cudaSuccess) e = cudaMemset(ps.counter, 0, 8);
         if (e == cudaSuccess) e = cudaMemset(ps.abort, 0, 4);
+        if (e == cudaSuccess) e = cudaMemset(ps.front, 0, 16);
         if (e == cudaSuccess) e = cudaMemset(c->psi_alt, 0, (size_t)nv * 2 * szc);
         H2D((void *)ps.dep_f, dep_f.data(), (size_t)NC * 8);
         H2D((void *)ps.dep_d, dep_d.data(), (size_t)NC * 8);

@@ -66,6 +66,7 @@ constexpr int kPipeMaxPolls = 1 << 21; // polls of a flag range before giving up
 struct PipeState {
     int *flag_f;                 // [n_chunks] epoch at which F of the chunk finished
     int *flag_d;                 // [n_chunks] epoch at which D of the chunk finished
+    unsigned long long *front;   // [2] per phase: (epoch << 32) | first chunk not known done
     const int2 *dep_f;           // [n_chunks] chunk range whose F a chunk's D reads
     const int2 *dep_d;           // [n_chunks] chunk range whose D a wall chunk's W reads
     const int *wstart;           // [n_chunks + 1] wall index range of each wall chunk

@@ -167,25 +167,54 @@ __device__ __forceinline__ typename Traits<TS>::C ref_of(const DevState &s, int 
     return wgt<C>(i) * (C)(sigma == 0 ? s.rref1 : s.rref2);
 }
 
+// Offset of slot_j(x) inside one component's population block when x + e_j
+// is not beyond an open plane (the caller handles that case).
+template <int P>
+__device__ __forceinline__ unsigned slot_in_block(int j, int n, uint32_t pv, const Nbr &b, const DevState &s)
+{
+    const unsigned np = (unsigned)s.npad;
+    if (P == 0) return (unsigned)opp(j) * np + (unsigned)n;
+    const int c = __ldg(s.cidx + ((int)pv + nb_off(j, b)));
+    return c >= 0 ? (unsigned)j * np + (unsigned)c : (unsigned)opp(j) * np + (unsigned)n;
+}
+
+// Offset of the boundary cell that replaces slot_j(x) for a direction j
+// leaving through an open plane, inside one component's boundary block.
+__device__ __forceinline__ unsigned bc_cell(int j, uint32_t pv, uint32_t fl, const DevState &s)
+{
+    const int plane = (fl & F_INLET) ? 0 : 1;
+    const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
+    return (unsigned)((plane * 10 + miss_k(opp(j))) * s.nxy + p);
+}
+
+template <typename TS, bool L2ONLY>
+__device__ __forceinline__ typename Traits<TS>::C ld_pop(const TS *p, typename Traits<TS>::C ref)
+{
+    return L2ONLY ? Traits<TS>::load_cg(p, ref) : Traits<TS>::load(p, ref);
+}
+
 // Post-stream populations f[sigma][i] of node n at parity P.  L2ONLY loads
 // bypass L1 (for data written earlier in the same launch).
 template <typename TS, int P, bool L2ONLY = false>
 __device__ __forceinline__ void load_pops(typename Traits<TS>::C f[2][19], int n, uint32_t pv, uint32_t fl,
                                           const Nbr &b, const DevState &s)
 {
-    const TS *A = reinterpret_cast<const TS *>(s.f);
-#pragma unroll
-    for (int sg = 0; sg < 2; ++sg) {
-        const TS *p = A + (long long)sg * 19 * s.npad + n;
-        f[sg][0] = L2ONLY ? Traits<TS>::load_cg(p, ref_of<TS>(s, sg, 0)) : Traits<TS>::load(p, ref_of<TS>(s, sg, 0));
-    }
+    const TS *A0 = reinterpret_cast<const TS *>(s.f);
+    const TS *A1 = A0 + 19 * s.npad;
+    const bool plane = P == 1 && (fl & (F_INLET | F_OUTLET));
+    f[0][0] = ld_pop<TS, L2ONLY>(A0 + n, ref_of<TS>(s, 0, 0));
+    f[1][0] = ld_pop<TS, L2ONLY>(A1 + n, ref_of<TS>(s, 1, 0));
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
-        const int sl = slot_of<P>(j, n, pv, fl, b, s);
-#pragma unroll
-        for (int sg = 0; sg < 2; ++sg) {
-            const TS *p = cell<TS>(s, sg, sl);
-            f[sg][opp(j)] = L2ONLY ? Traits<TS>::load_cg(p, ref_of<TS>(s, sg, j)) : Traits<TS>::load(p, ref_of<TS>(s, sg, j));
+        if (ez(j) != 0 && plane && outside(j, fl)) {
+            const TS *B0 = reinterpret_cast<const TS *>(s.bc);
+            const unsigned q = bc_cell(j, pv, fl, s);
+            f[0][opp(j)] = ld_pop<TS, L2ONLY>(B0 + q, ref_of<TS>(s, 0, j));
+            f[1][opp(j)] = ld_pop<TS, L2ONLY>(B0 + 5 * s.nxy + q, ref_of<TS>(s, 1, j));
+        } else {
+            const unsigned q = slot_in_block<P>(j, n, pv, b, s);
+            f[0][opp(j)] = ld_pop<TS, L2ONLY>(A0 + q, ref_of<TS>(s, 0, j));
+            f[1][opp(j)] = ld_pop<TS, L2ONLY>(A1 + q, ref_of<TS>(s, 1, j));
         }
     }
 }
@@ -195,15 +224,17 @@ template <typename TS, int P>
 __device__ __forceinline__ void store_pops(const typename Traits<TS>::C f[2][19], int n, uint32_t pv, uint32_t fl,
                                            const Nbr &b, const DevState &s)
 {
-    TS *A = reinterpret_cast<TS *>(s.f);
-#pragma unroll
-    for (int sg = 0; sg < 2; ++sg) Traits<TS>::store(A + (long long)sg * 19 * s.npad + n, f[sg][0], ref_of<TS>(s, sg, 0));
+    TS *A0 = reinterpret_cast<TS *>(s.f);
+    TS *A1 = A0 + 19 * s.npad;
+    const bool plane = P == 1 && (fl & (F_INLET | F_OUTLET));
+    Traits<TS>::store(A0 + n, f[0][0], ref_of<TS>(s, 0, 0));
+    Traits<TS>::store(A1 + n, f[1][0], ref_of<TS>(s, 1, 0));
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
-        if (P == 1 && outside(j, fl)) continue;  // leaves the domain
-        const int sl = slot_of<P>(j, n, pv, fl, b, s);
-#pragma unroll
-        for (int sg = 0; sg < 2; ++sg) Traits<TS>::store(cell<TS>(s, sg, sl), f[sg][j], ref_of<TS>(s, sg, j));
+        if (ez(j) != 0 && plane && outside(j, fl)) continue;  // leaves the domain
+        const unsigned q = slot_in_block<P>(j, n, pv, b, s);
+        Traits<TS>::store(A0 + q, f[0][j], ref_of<TS>(s, 0, j));
+        Traits<TS>::store(A1 + q, f[1][j], ref_of<TS>(s, 1, j));
     }
 }
 
@@ -375,7 +406,7 @@ __global__ void __launch_bounds__(256) k_wall(DevState s)
 }
 
 template <typename TS, int P>
-__global__ void __launch_bounds__(256) k_fused(DevState s)
+__global__ void __launch_bounds__(256, 3) k_fused(DevState s)
 {
     using C = typename Traits<TS>::C;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;

@@ -40,35 +40,54 @@ __device__ __forceinline__ void publish(int *flags, int c, int epoch)
     }
 }
 
-// Wait until flags[r.x .. r.y] all reach epoch.  Warp 0 polls; the result is
-// shared with the block.  Returns false after a timeout or an abort.
-__device__ __forceinline__ bool wait_flags(const int *flags, int2 r, int epoch, const PipeState &ps, int *sh_ok)
+__device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p)
 {
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        bool ok = false;
-        for (int it = 0; it < kPipeMaxPolls; ++it) {
-            bool mine = true;
-            for (int m = r.x + lane; m <= r.y; m += 32)
-                if (ld_acquire(flags + m) < epoch) {
-                    mine = false;
-                    break;
-                }
-            ok = __all_sync(0xffffffffu, mine);
-            if (ok) break;
-            if (*(volatile int *)ps.abort) break;
-            __nanosleep(64);
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Wait until every chunk <= hi of a phase has published `epoch` in flags.
+// front holds (epoch << 32) | f, meaning all chunks below f are known done in
+// that epoch; the fast path is one load of it.  Otherwise the whole block
+// scans flags[f .. hi] with independent acquire loads, advances front to the
+// first chunk not done (atomicMax: front only grows), and retries after a
+// short sleep.  Returns false after a timeout or an abort (block-uniform).
+__device__ __forceinline__ bool wait_upto(const int *flags, unsigned long long *front, int hi, int epoch,
+                                          const PipeState &ps, int *sh)
+{
+    const unsigned long long tag = (unsigned long long)(unsigned)epoch << 32;
+    for (int it = 0; it < kPipeMaxPolls; ++it) {
+        if (threadIdx.x == 0) {
+            const unsigned long long f = ld_acquire64(front);
+            sh[0] = (f & 0xffffffff00000000ULL) == tag ? (int)(f & 0xffffffffULL) : 0;
+            sh[1] = 0x7fffffff;
+            sh[2] = *(volatile int *)ps.abort;
         }
-        if (lane == 0) {
-            *sh_ok = ok ? 1 : 0;
-            if (!ok) {
-                atomicExch(ps.abort, 1);
-                atomicOr(ps.status, 4);
-            }
+        __syncthreads();
+        const int lo = sh[0];
+        if (lo > hi) return true;
+        if (sh[2]) break;
+        int bad = 0x7fffffff;
+        for (int m = lo + threadIdx.x; m <= hi; m += blockDim.x)
+            if (ld_acquire(flags + m) < epoch) bad = min(bad, m);
+        if (bad != 0x7fffffff) atomicMin(&sh[1], bad);
+        __syncthreads();
+        const int first_bad = sh[1];
+        if (threadIdx.x == 0) atomicMax(front, tag | (unsigned)(first_bad == 0x7fffffff ? hi + 1 : first_bad));
+        if (first_bad == 0x7fffffff) {
+            __syncthreads();  // sh is rewritten by the next call
+            return true;
         }
+        __nanosleep(128);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        atomicExch(ps.abort, 1);
+        atomicOr(ps.status, 4);
     }
     __syncthreads();
-    return *sh_ok != 0;
+    return false;
 }
 
 // F: the fused force / collision / streaming update of one node (the body of
@@ -155,7 +174,7 @@ template <typename TS, int P>
 __global__ void __launch_bounds__(kChunk, PipeOcc<TS>::blocks) k_pipe(DevState s, PipeState ps)
 {
     __shared__ int sh_k;
-    __shared__ int sh_ok;
+    __shared__ int sh_w[3];
     for (;;) {
         if (threadIdx.x == 0)
             sh_k = *(volatile int *)ps.abort ? ps.tickets : (int)(atomicAdd(ps.counter, 1ULL) - ps.base);
@@ -169,14 +188,14 @@ __global__ void __launch_bounds__(kChunk, PipeOcc<TS>::blocks) k_pipe(DevState s
         }
         const int c = k - ps.lag_d;
         if (c >= 0 && c < ps.n_chunks) {
-            if (!wait_flags(ps.flag_f, ps.dep_f[c], ps.epoch, ps, &sh_ok)) return;
+            if (!wait_upto(ps.flag_f, ps.front, ps.dep_f[c].y, ps.epoch, ps, sh_w)) return;
             const int n = c * kChunk + threadIdx.x;
             if (n < s.n_fluid) dens_node<TS, 1 - P>(n, s, ps.psi_next);
             publish(ps.flag_d, c, ps.epoch);
         }
         const int cw = k - ps.lag_w;
         if (cw >= 0 && cw < ps.n_chunks) {
-            if (!wait_flags(ps.flag_d, ps.dep_d[cw], ps.epoch, ps, &sh_ok)) return;
+            if (!wait_upto(ps.flag_d, ps.front + 1, ps.dep_d[cw].y, ps.epoch, ps, sh_w)) return;
             for (int w = ps.wstart[cw] + threadIdx.x; w < ps.wstart[cw + 1]; w += kChunk) wall_node<TS>(w, s, ps.psi_next);
         }
         __syncthreads();  // sh_k is rewritten at the top

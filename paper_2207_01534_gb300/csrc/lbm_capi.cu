@@ -377,7 +377,7 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         wxi.push_back(g->xi_field ? (double)g->xi_field[v] : p->xi);
     }
     const int64_t NW = (int64_t)wpvox.size();
-    if (19 * (((N + 63) / 64) * 64 + 64) >= ((int64_t)1 << 31))
+    if (18 * (((N + 63) / 64) * 64 + 64) >= ((int64_t)1 << 31))
         return fail(nullptr, LBM_ERR_UNSUPPORTED, "more than 113 million fluid nodes in one context");
 
     lbm_ctx *c = new lbm_ctx();
@@ -431,7 +431,8 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         if (!q) ok = false;
         return q;
     };
-    s.f = A((size_t)2 * 19 * npad * sz);
+    s.f = A((size_t)18 * npad * 2 * sz);    // moving pairs M[18][npad]
+    s.rest = A((size_t)npad * 2 * szc);      // rest pairs R[npad]
     void *d_pvox = A((size_t)N * 4);
     void *d_nflags = A((size_t)N);
     void *d_cidx = A((size_t)nv * 4);
@@ -563,7 +564,8 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     H2D(d_wmask, wmask.data(), (size_t)NW * 4);
     H2D(d_winv, winv_h, (size_t)NW * szc);
     H2D(d_wxi, wxi_h, (size_t)NW * szc);
-    if (e == cudaSuccess) e = cudaMemset(s.f, 0, (size_t)2 * 19 * npad * sz);
+    if (e == cudaSuccess) e = cudaMemset(s.f, 0, (size_t)18 * npad * 2 * sz);
+    if (e == cudaSuccess) e = cudaMemset(s.rest, 0, (size_t)npad * 2 * szc);
     if (e == cudaSuccess) e = cudaMemset(s.psi, 0, (size_t)nv * 2 * szc);
     if (e == cudaSuccess && open_z) e = cudaMemset(s.bc, 0, (size_t)2 * 2 * 5 * nxy * sz);
     if (e == cudaSuccess && open_z) e = cudaMemset(c->d_frozen, 0, (size_t)2 * 5 * nxy * 8);

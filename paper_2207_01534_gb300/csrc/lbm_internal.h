@@ -20,9 +20,11 @@ constexpr int kWallFaceShift = 24;
 
 // Everything a kernel needs, passed by value.
 struct DevState {
-    // populations: storage type, [sigma][i][Npad], SoA
+    // populations: moving pairs M[18][npad] (storage type) and rest pairs
+    // R[npad] (compute precision); see lbm_kernels.cuh
     void *f;
-    int64_t npad;            // stride between direction arrays (multiple of 64)
+    void *rest;
+    int64_t npad;            // stride between direction rows (multiple of 64)
     int32_t n_fluid;
     const uint32_t *pvox;    // [n_fluid] voxel index v = x + nx*(y + ny*z)
     const uint8_t *nflags;   // [n_fluid]
@@ -37,9 +39,10 @@ struct DevState {
     const uint32_t *wmask;   // [n_wall] bit i: direction i leads to an in-domain fluid voxel; face bits << 24
     const void *winv;        // [n_wall] 1 / sum of w_i over those directions (Eq. 15 denominator), compute type
     const void *wxi;         // [n_wall] xi at the wall voxel, compute type
-    // open planes (z): bc slots hold the missing populations of the odd-parity layout,
-    // [plane][sigma][k][nxy] in the storage type; frozen holds the initial values of
-    // the non-prescribed component's missing populations, [plane][k][nxy] (double).
+    // open planes (z): bc cells hold the missing population pairs of the
+    // odd-parity layout, [plane][k][nxy] in the storage type; frozen holds the
+    // initial values of the non-prescribed component's missing populations,
+    // [plane][k][nxy] (double).
     int32_t open_z;
     void *bc;
     const double *frozen;

@@ -3,22 +3,25 @@
 // unit per population storage type.
 //
 // Data layout (all in device memory):
-//   populations  A[sigma][i][npad]  SoA over the compact fluid index n, stored
-//                in place with the A-A pattern: one copy of every population.
-//   psi          dense (psi1, psi2) pairs over all nx*ny*nz voxels: rho^sigma
-//                on fluid voxels (Eq. 3 / 11), rho-tilde^sigma on wall voxels
-//                (Eqs. 14-15), so the force stencil needs no neighbour table.
-//   cidx         dense compact index (-1 on solids) for the streaming partner.
+//   rest   R[npad]        pairs (f_0^(1), f_0^(2)) of the rest population per
+//                         fluid node (compact index n);
+//   moving M[18][npad]    pairs (f_i^(1), f_i^(2)), i = 1..18, SoA over n and
+//                         stored in place with the A-A pattern (one copy).  The
+//                         two components of a direction sit side by side, so
+//                         every access moves both with one 8-byte (FP32) load
+//                         or store and the arithmetic runs on packed pairs;
+//   psi    dense (psi1, psi2) pairs over all nx*ny*nz voxels: rho^sigma on fluid
+//          voxels (Eqs. 3, 11), rho-tilde^sigma on wall voxels (Eqs. 14-15), so
+//          the force stencil needs no neighbour table;
+//   cidx   dense compact index (-1 on solids) for the streaming partner.
 //
-// A-A slots.  Define slot_j(x), j = 1..18, as the storage cell that holds the
-// post-stream population f_opp(j)(x) when a step starts and that receives the
-// post-collision f*_j(x) when the step ends.  On even steps slot_j(x) =
-// A[opp(j)][x] (everything local); on odd steps slot_j(x) = A[j][x + e_j] when
-// x + e_j is fluid, A[opp(j)][x] when it is solid (half-way bounce-back), and a
-// boundary cell bc[...] when x + e_j lies beyond an open plane.  The rest
-// population always lives in A[0][x].  Every cell belongs to exactly one
-// (node, direction) on a given parity, so a node's reads and writes never race
-// with another node's.
+// A-A slots.  Define slot_j(x), j = 1..18, as the pair cell that holds the
+// post-stream f_opp(j)(x) when a step starts and receives the post-collision
+// f*_j(x) when it ends.  On even steps slot_j(x) = M[opp(j)][x] (all local); on
+// odd steps slot_j(x) = M[j][x + e_j] when x + e_j is fluid, M[opp(j)][x] when
+// it is solid (half-way bounce-back), and a boundary cell when x + e_j lies
+// beyond an open plane.  Every cell belongs to exactly one (node, direction)
+// on a given parity, so a node's reads and writes never race with another's.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -77,7 +80,37 @@ __host__ __device__ constexpr C wgt(int i)
 }
 
 // ---------------------------------------------------------------------------
-// Storage traits: how a population is kept in memory.
+// Pair arithmetic: (component 1, component 2) in one register pair.  FP32
+// pairs use the packed FP32 instructions of sm_100+ (one instruction for both
+// lanes); FP64 pairs are two scalar operations.
+__device__ __forceinline__ float2 mk2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ double2 mk2(double a, double b) { return make_double2(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ double2 add2(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 mul2(double2 a, double2 b) { return make_double2(a.x * b.x, a.y * b.y); }
+__device__ __forceinline__ double2 fma2(double2 a, double2 b, double2 c)
+{
+    return make_double2(fma(a.x, b.x, c.x), fma(a.y, b.y, c.y));
+}
+template <typename C2>
+__device__ __forceinline__ C2 sub2(C2 a, C2 b)  // a - b
+{
+    using C = decltype(a.x);
+    return fma2(b, mk2(C(-1), C(-1)), a);
+}
+template <typename C2>
+__device__ __forceinline__ C2 bc2(decltype(C2{}.x) k)  // (k, k)
+{
+    return mk2(k, k);
+}
+
+// ---------------------------------------------------------------------------
+// Storage traits: how population pairs are kept in memory.  C / C2 are the
+// compute scalar and pair; S2 the stored pair of a moving population; R2 the
+// stored pair of the rest population.  ref is the per-direction offset
+// (w_i rho_ref^1, w_i rho_ref^2) that deviation storage subtracts.
 template <typename TS>
 struct Traits;
 
@@ -85,19 +118,49 @@ template <>
 struct Traits<float> {
     using C = float;
     using C2 = float2;
-    __device__ static __forceinline__ float load(const float *p, float) { return __ldg(p); }
-    __device__ static __forceinline__ float load_cg(const float *p, float) { return __ldcg(p); }
-    __device__ static __forceinline__ void store(float *p, float v, float) { *p = v; }
+    using S2 = float2;
+    using R2 = float2;
+    static constexpr bool kDev = false;
+    __device__ static __forceinline__ C2 load(const S2 *p, C2) { return __ldg(p); }
+    __device__ static __forceinline__ C2 load_cg(const S2 *p, C2) { return __ldcg(p); }
+    __device__ static __forceinline__ void store(S2 *p, C2 v, C2) { *p = v; }
+    __device__ static __forceinline__ void store1(S2 *p, int sg, C v, C) { (sg ? p->y : p->x) = v; }
 };
 
 template <>
 struct Traits<double> {
     using C = double;
     using C2 = double2;
-    __device__ static __forceinline__ double load(const double *p, double) { return __ldg(p); }
-    __device__ static __forceinline__ double load_cg(const double *p, double) { return __ldcg(p); }
-    __device__ static __forceinline__ void store(double *p, double v, double) { *p = v; }
+    using S2 = double2;
+    using R2 = double2;
+    static constexpr bool kDev = false;
+    __device__ static __forceinline__ C2 load(const S2 *p, C2) { return __ldg(p); }
+    __device__ static __forceinline__ C2 load_cg(const S2 *p, C2) { return __ldcg(p); }
+    __device__ static __forceinline__ void store(S2 *p, C2 v, C2) { *p = v; }
+    __device__ static __forceinline__ void store1(S2 *p, int sg, C v, C) { (sg ? p->y : p->x) = v; }
 };
+
+template <typename TS>
+__device__ __forceinline__ typename Traits<TS>::C2 ref_of(const DevState &s, int i)
+{
+    using C = typename Traits<TS>::C;
+    if (!Traits<TS>::kDev) return mk2(C(0), C(0));
+    return mk2(wgt<C>(i) * (C)s.rref1, wgt<C>(i) * (C)s.rref2);
+}
+
+// Rest-population pair of node n (kept at compute precision: FP32 for the
+// 16-bit storage forms).
+template <typename TS, bool L2ONLY>
+__device__ __forceinline__ typename Traits<TS>::C2 ld_rest(const DevState &s, int n)
+{
+    const typename Traits<TS>::R2 *R = reinterpret_cast<const typename Traits<TS>::R2 *>(s.rest);
+    return L2ONLY ? __ldcg(R + n) : __ldg(R + n);
+}
+template <typename TS>
+__device__ __forceinline__ void st_rest(const DevState &s, int n, typename Traits<TS>::C2 v)
+{
+    reinterpret_cast<typename Traits<TS>::R2 *>(s.rest)[n] = v;
+}
 
 // ---------------------------------------------------------------------------
 // Geometry helpers
@@ -137,220 +200,174 @@ __device__ __forceinline__ bool outside(int j, uint32_t fl)
     return (ez(j) < 0 && (fl & F_INLET)) || (ez(j) > 0 && (fl & F_OUTLET));
 }
 
-// slot_j(x) as an offset into one component's population block (>= 0;
-// 19 * npad < 2^31 is checked at creation) or as -1 - (offset into one
-// component's boundary block).
-template <int P>
-__device__ __forceinline__ int slot_of(int j, int n, uint32_t pv, uint32_t fl, const Nbr &b, const DevState &s)
-{
-    if (P == 0) return opp(j) * (int)s.npad + n;
-    if (outside(j, fl)) {
-        const int plane = (fl & F_INLET) ? 0 : 1;
-        const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
-        return -1 - ((plane * 10 + miss_k(opp(j))) * s.nxy + p);
-    }
-    const int c = __ldg(s.cidx + ((int)pv + nb_off(j, b)));
-    return c >= 0 ? j * (int)s.npad + c : opp(j) * (int)s.npad + n;
-}
-
-template <typename TS>
-__device__ __forceinline__ TS *cell(const DevState &s, int sigma, int slot)
-{
-    return slot >= 0 ? reinterpret_cast<TS *>(s.f) + (long long)sigma * 19 * s.npad + slot
-                     : reinterpret_cast<TS *>(s.bc) + (long long)sigma * 5 * s.nxy + (-1 - slot);
-}
-
-template <typename TS>
-__device__ __forceinline__ typename Traits<TS>::C ref_of(const DevState &s, int sigma, int i)
-{
-    using C = typename Traits<TS>::C;
-    return wgt<C>(i) * (C)(sigma == 0 ? s.rref1 : s.rref2);
-}
-
-// Offset of slot_j(x) inside one component's population block when x + e_j
-// is not beyond an open plane (the caller handles that case).
+// Pair offset of slot_j(x) in the moving block when x + e_j is not beyond an
+// open plane (18 * npad < 2^31 is checked at creation).
 template <int P>
 __device__ __forceinline__ unsigned slot_in_block(int j, int n, uint32_t pv, const Nbr &b, const DevState &s)
 {
     const unsigned np = (unsigned)s.npad;
-    if (P == 0) return (unsigned)opp(j) * np + (unsigned)n;
+    if (P == 0) return (unsigned)(opp(j) - 1) * np + (unsigned)n;
     const int c = __ldg(s.cidx + ((int)pv + nb_off(j, b)));
-    return c >= 0 ? (unsigned)j * np + (unsigned)c : (unsigned)opp(j) * np + (unsigned)n;
+    return c >= 0 ? (unsigned)(j - 1) * np + (unsigned)c : (unsigned)(opp(j) - 1) * np + (unsigned)n;
 }
 
-// Offset of the boundary cell that replaces slot_j(x) for a direction j
-// leaving through an open plane, inside one component's boundary block.
+// Pair offset of the boundary cell that replaces slot_j(x) when j leaves the
+// domain through an open plane: bc[plane][k][nxy], k = the missing direction.
 __device__ __forceinline__ unsigned bc_cell(int j, uint32_t pv, uint32_t fl, const DevState &s)
 {
     const int plane = (fl & F_INLET) ? 0 : 1;
     const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
-    return (unsigned)((plane * 10 + miss_k(opp(j))) * s.nxy + p);
+    return (unsigned)((plane * 5 + miss_k(opp(j))) * s.nxy + p);
 }
 
-template <typename TS, bool L2ONLY>
-__device__ __forceinline__ typename Traits<TS>::C ld_pop(const TS *p, typename Traits<TS>::C ref)
+template <typename TS, int P>
+__device__ __forceinline__ typename Traits<TS>::S2 *slot_ptr(int j, int n, uint32_t pv, uint32_t fl, const Nbr &b,
+                                                            const DevState &s)
 {
-    return L2ONLY ? Traits<TS>::load_cg(p, ref) : Traits<TS>::load(p, ref);
+    using S2 = typename Traits<TS>::S2;
+    if (P == 1 && ez(j) != 0 && outside(j, fl)) return reinterpret_cast<S2 *>(s.bc) + bc_cell(j, pv, fl, s);
+    return reinterpret_cast<S2 *>(s.f) + slot_in_block<P>(j, n, pv, b, s);
 }
 
-// Post-stream populations f[sigma][i] of node n at parity P.  L2ONLY loads
+// Post-stream population pairs f[i] of node n at parity P.  L2ONLY loads
 // bypass L1 (for data written earlier in the same launch).
 template <typename TS, int P, bool L2ONLY = false>
-__device__ __forceinline__ void load_pops(typename Traits<TS>::C f[2][19], int n, uint32_t pv, uint32_t fl,
+__device__ __forceinline__ void load_pops(typename Traits<TS>::C2 f[19], int n, uint32_t pv, uint32_t fl,
                                           const Nbr &b, const DevState &s)
 {
-    const TS *A0 = reinterpret_cast<const TS *>(s.f);
-    const TS *A1 = A0 + 19 * s.npad;
+    using S2 = typename Traits<TS>::S2;
+    const S2 *M = reinterpret_cast<const S2 *>(s.f);
+    const S2 *B = reinterpret_cast<const S2 *>(s.bc);
     const bool plane = P == 1 && (fl & (F_INLET | F_OUTLET));
-    f[0][0] = ld_pop<TS, L2ONLY>(A0 + n, ref_of<TS>(s, 0, 0));
-    f[1][0] = ld_pop<TS, L2ONLY>(A1 + n, ref_of<TS>(s, 1, 0));
+    f[0] = ld_rest<TS, L2ONLY>(s, n);
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
-        if (ez(j) != 0 && plane && outside(j, fl)) {
-            const TS *B0 = reinterpret_cast<const TS *>(s.bc);
-            const unsigned q = bc_cell(j, pv, fl, s);
-            f[0][opp(j)] = ld_pop<TS, L2ONLY>(B0 + q, ref_of<TS>(s, 0, j));
-            f[1][opp(j)] = ld_pop<TS, L2ONLY>(B0 + 5 * s.nxy + q, ref_of<TS>(s, 1, j));
-        } else {
-            const unsigned q = slot_in_block<P>(j, n, pv, b, s);
-            f[0][opp(j)] = ld_pop<TS, L2ONLY>(A0 + q, ref_of<TS>(s, 0, j));
-            f[1][opp(j)] = ld_pop<TS, L2ONLY>(A1 + q, ref_of<TS>(s, 1, j));
-        }
+        const S2 *p = (ez(j) != 0 && plane && outside(j, fl)) ? B + bc_cell(j, pv, fl, s)
+                                                               : M + slot_in_block<P>(j, n, pv, b, s);
+        f[opp(j)] = L2ONLY ? Traits<TS>::load_cg(p, ref_of<TS>(s, j)) : Traits<TS>::load(p, ref_of<TS>(s, j));
     }
 }
 
-// Post-collision populations f[sigma][i] of node n into their slots.
+// Post-collision population pairs f[i] of node n into their slots.
 template <typename TS, int P>
-__device__ __forceinline__ void store_pops(const typename Traits<TS>::C f[2][19], int n, uint32_t pv, uint32_t fl,
+__device__ __forceinline__ void store_pops(const typename Traits<TS>::C2 f[19], int n, uint32_t pv, uint32_t fl,
                                            const Nbr &b, const DevState &s)
 {
-    TS *A0 = reinterpret_cast<TS *>(s.f);
-    TS *A1 = A0 + 19 * s.npad;
+    using S2 = typename Traits<TS>::S2;
+    S2 *M = reinterpret_cast<S2 *>(s.f);
     const bool plane = P == 1 && (fl & (F_INLET | F_OUTLET));
-    Traits<TS>::store(A0 + n, f[0][0], ref_of<TS>(s, 0, 0));
-    Traits<TS>::store(A1 + n, f[1][0], ref_of<TS>(s, 1, 0));
+    st_rest<TS>(s, n, f[0]);
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
         if (ez(j) != 0 && plane && outside(j, fl)) continue;  // leaves the domain
-        const unsigned q = slot_in_block<P>(j, n, pv, b, s);
-        Traits<TS>::store(A0 + q, f[0][j], ref_of<TS>(s, 0, j));
-        Traits<TS>::store(A1 + q, f[1][j], ref_of<TS>(s, 1, j));
+        Traits<TS>::store(M + slot_in_block<P>(j, n, pv, b, s), f[j], ref_of<TS>(s, j));
     }
 }
 
-template <typename C>
-__device__ __forceinline__ C sum19(const C f[19])
+// rho^sigma = sum_i f_i^sigma (Eq. 3), in direction order for both components.
+template <typename C2>
+__device__ __forceinline__ C2 sum19(const C2 f[19])
 {
-    C r = f[0];
+    C2 r = f[0];
 #pragma unroll
-    for (int i = 1; i < 19; ++i) r += f[i];
+    for (int i = 1; i < 19; ++i) r = add2(r, f[i]);
     return r;
 }
 
-// Force of Eqs. 10, 11, 13: F^sigma = -G psi^sigma(x) sum_i w_i psi^sigma-bar(x+e_i) e_i
-// (+ rho^sigma g), psi being rho on fluid and rho-tilde on wall voxels; beyond
-// an open plane the mirrored direction's neighbour is used (Section 2).
+// Force of Eqs. 10, 11, 13 for both components:
+// F^sigma = -G psi^sigma(x) sum_i w_i psi^sigma-bar(x+e_i) e_i + rho^sigma g,
+// psi being rho on fluid and rho-tilde on wall voxels; beyond an open plane the
+// mirrored direction's neighbour is used (Section 2).  The stencil sums
+// neighbour minus own value (the same sum, since sum_i w_i e_i = 0, with far
+// less cancellation error in FP32).
 template <typename TS>
-__device__ __forceinline__ void forces(typename Traits<TS>::C rho1, typename Traits<TS>::C rho2, uint32_t pv,
-                                       uint32_t fl, const Nbr &b, const DevState &s, typename Traits<TS>::C F1[3],
-                                       typename Traits<TS>::C F2[3])
+__device__ __forceinline__ void forces(typename Traits<TS>::C2 rho, uint32_t pv, uint32_t fl, const Nbr &b,
+                                       const DevState &s, typename Traits<TS>::C2 F[3])
 {
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
-    const C2 *psi = reinterpret_cast<const C2 *>(s.psi);
-    C a1[3] = {0, 0, 0}, a2[3] = {0, 0, 0};
+    const C2 *psi = reinterpret_cast<const C2 *>(s.psi) + pv;
+    C2 a[3] = {mk2(C(0), C(0)), mk2(C(0), C(0)), mk2(C(0), C(0))};
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
-        const int off = outside(j, fl) ? nb_off(mirz(j), b) : nb_off(j, b);
-        // neighbour minus own value: the same sum, since sum_j w_j e_j = 0,
-        // with far less cancellation error in FP32 near uniform regions
-        const C2 q = psi[(int)pv + off];
-        const C d1 = q.x - rho1, d2 = q.y - rho2;
+        const int off = (ez(j) != 0 && outside(j, fl)) ? nb_off(mirz(j), b) : nb_off(j, b);
+        const C2 d = sub2(psi[off], rho);
         const C w = wgt<C>(j);
-        if (ex(j)) { a1[0] += (w * ex(j)) * d1; a2[0] += (w * ex(j)) * d2; }
-        if (ey(j)) { a1[1] += (w * ey(j)) * d1; a2[1] += (w * ey(j)) * d2; }
-        if (ez(j)) { a1[2] += (w * ez(j)) * d1; a2[2] += (w * ez(j)) * d2; }
+        if (ex(j)) a[0] = fma2(bc2<C2>(w * ex(j)), d, a[0]);
+        if (ey(j)) a[1] = fma2(bc2<C2>(w * ey(j)), d, a[1]);
+        if (ez(j)) a[2] = fma2(bc2<C2>(w * ez(j)), d, a[2]);
     }
-    const C G = (C)s.G;
+    const C mG = -(C)s.G;
     const C g[3] = {(C)s.gx, (C)s.gy, (C)s.gz};
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        F1[a] = -G * rho1 * a2[a] + rho1 * g[a];
-        F2[a] = -G * rho2 * a1[a] + rho2 * g[a];
-    }
+    for (int k = 0; k < 3; ++k) F[k] = mul2(rho, fma2(bc2<C2>(mG), mk2(a[k].y, a[k].x), bc2<C2>(g[k])));
 }
 
 // Eqs. 6-8: tau_s = sum rho^sigma tau^sigma / rho (nu = c_s^2 (tau - 1/2));
 // u = (sum_sigma sum_i e_i f_i^sigma [+ F^sigma / 2]) / rho.
-template <typename C>
-__device__ __forceinline__ void mix_velocity(const C f[2][19], C rho1, C rho2, const C F1[3], const C F2[3],
-                                             const DevState &s, C &inv_rho, C u[3])
+template <typename C, typename C2>
+__device__ __forceinline__ void mix_velocity(const C2 f[19], C2 rho, const C2 F[3], const DevState &s, C &inv_rho,
+                                             C u[3])
 {
-    C m[3] = {0, 0, 0};
+    C2 m[3] = {mk2(C(0), C(0)), mk2(C(0), C(0)), mk2(C(0), C(0))};
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        const C t = f[0][i] + f[1][i];
-        if (ex(i)) m[0] += ex(i) * t;
-        if (ey(i)) m[1] += ey(i) * t;
-        if (ez(i)) m[2] += ez(i) * t;
+        if (ex(i)) m[0] = ex(i) > 0 ? add2(m[0], f[i]) : sub2(m[0], f[i]);
+        if (ey(i)) m[1] = ey(i) > 0 ? add2(m[1], f[i]) : sub2(m[1], f[i]);
+        if (ez(i)) m[2] = ez(i) > 0 ? add2(m[2], f[i]) : sub2(m[2], f[i]);
     }
-    inv_rho = C(1) / (rho1 + rho2);
+    inv_rho = C(1) / (rho.x + rho.y);
     const C h = s.velocity_shift ? C(0.5) : C(0);
 #pragma unroll
-    for (int a = 0; a < 3; ++a) u[a] = (m[a] + h * (F1[a] + F2[a])) * inv_rho;
+    for (int k = 0; k < 3; ++k) {
+        const C2 t = fma2(bc2<C2>(h), F[k], m[k]);
+        u[k] = (t.x + t.y) * inv_rho;
+    }
 }
 
-// Eq. 1 with Eq. 2 equilibrium and Eq. 9 forcing, in place on f[sigma][i]:
+// Eq. 1 with Eq. 2 equilibrium and Eq. 9 forcing, in place on the pairs f[i]:
 // f* = (1 - 1/tau_s) f + f^eq / tau_s + (1 - 1/(2 tau_s)) S.  Directions are
 // taken in opposite pairs (i, opp(i)): with eu = e_i.u and eF = e_i.F, the
-// pair shares sym = 1 + 4.5 eu^2 - 1.5 u^2 and 9 eu eF - 3 u.F, and differs
+// pair shares sym = 1 + 4.5 eu^2 - 1.5 u^2 and 9 eu eF - 3 u.F and differs
 // only in the sign of 3 eu and 3 eF, so each pair is computed once.
-template <typename C>
-__device__ __forceinline__ void collide(C f[2][19], C rho1, C rho2, C inv_rho, const C u[3], const C F1[3],
-                                        const C F2[3], const DevState &s)
+template <typename C, typename C2>
+__device__ __forceinline__ void collide(C2 f[19], C2 rho, C inv_rho, const C u[3], const C2 F[3], const DevState &s)
 {
-    const C tau_s = (rho1 * (C)s.tau1 + rho2 * (C)s.tau2) * inv_rho;
+    const C tau_s = (rho.x * (C)s.tau1 + rho.y * (C)s.tau2) * inv_rho;
     const C om = C(1) / tau_s;
-    const C keep = C(1) - om;
+    const C2 keep = bc2<C2>(C(1) - om);
     const C cf = C(1) - C(0.5) * om;
     const C usq = C(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const C cuF1 = C(-3) * (u[0] * F1[0] + u[1] * F1[1] + u[2] * F1[2]);
-    const C cuF2 = C(-3) * (u[0] * F2[0] + u[1] * F2[1] + u[2] * F2[2]);
-    const C r1o = om * rho1, r2o = om * rho2;
-    // The rest population is written last as rho^sigma minus the 18 moving
-    // post-collision populations.  In exact arithmetic this equals Eq. 1 for
-    // i = 0 (sum_i f^eq_i = rho, sum_i S_i = 0); in FP32 it removes the mass
-    // bias of the rounded weights (their FP32 sum exceeds 1 by ~1.5e-8, which
-    // would otherwise create mass at every collision).
-    C sum1 = 0, sum2 = 0;
+    C2 uF = mul2(bc2<C2>(u[0]), F[0]);
+    uF = fma2(bc2<C2>(u[1]), F[1], uF);
+    uF = fma2(bc2<C2>(u[2]), F[2], uF);
+    const C2 cuF = mul2(bc2<C2>(C(-3)), uF);
+    const C2 ro = mul2(bc2<C2>(om), rho);
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
         if (opp(i) < i) continue;  // each pair once, from its first member
         const int o = opp(i);
         const C w = wgt<C>(i);
-        const C eu = ex(i) * u[0] + ey(i) * u[1] + ez(i) * u[2];
-        const C eF1 = ex(i) * F1[0] + ey(i) * F1[1] + ez(i) * F1[2];
-        const C eF2 = ex(i) * F2[0] + ey(i) * F2[1] + ez(i) * F2[2];
+        C eu = C(0);
+        C2 eF = mk2(C(0), C(0));
+        if (ex(i)) { eu += ex(i) * u[0]; eF = ex(i) > 0 ? add2(eF, F[0]) : sub2(eF, F[0]); }
+        if (ey(i)) { eu += ey(i) * u[1]; eF = ey(i) > 0 ? add2(eF, F[1]) : sub2(eF, F[1]); }
+        if (ez(i)) { eu += ez(i) * u[2]; eF = ez(i) > 0 ? add2(eF, F[2]) : sub2(eF, F[2]); }
         const C sym = C(1) + C(4.5) * eu * eu - usq;
-        const C ant = C(3) * eu;
-        const C A1 = w * (r1o * sym + cf * (C(9) * eu * eF1 + cuF1));
-        const C B1 = w * (r1o * ant + cf * C(3) * eF1);
-        const C A2 = w * (r2o * sym + cf * (C(9) * eu * eF2 + cuF2));
-        const C B2 = w * (r2o * ant + cf * C(3) * eF2);
-        f[0][i] = keep * f[0][i] + (A1 + B1);
-        f[0][o] = keep * f[0][o] + (A1 - B1);
-        f[1][i] = keep * f[1][i] + (A2 + B2);
-        f[1][o] = keep * f[1][o] + (A2 - B2);
+        const C2 A = mul2(bc2<C2>(w), fma2(ro, bc2<C2>(sym), mul2(bc2<C2>(cf), fma2(bc2<C2>(C(9) * eu), eF, cuF))));
+        const C2 B = mul2(bc2<C2>(w), fma2(ro, bc2<C2>(C(3) * eu), mul2(bc2<C2>(C(3) * cf), eF)));
+        f[i] = fma2(keep, f[i], add2(A, B));
+        f[o] = fma2(keep, f[o], sub2(A, B));
     }
-    // accumulated one direction at a time, in direction order: summing each
-    // pair first biases the FP32 rounding and drifts the mass measurably
+    // The rest population is written last as rho^sigma minus the 18 moving
+    // post-collision populations, accumulated in direction order.  In exact
+    // arithmetic this equals Eq. 1 for i = 0 (sum_i f^eq_i = rho, sum_i S_i =
+    // 0); in FP32 it removes the mass bias of the rounded weights (their FP32
+    // sum exceeds 1 by ~1.5e-8).
+    C2 sum = f[1];
 #pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        sum1 += f[0][i];
-        sum2 += f[1][i];
-    }
-    f[0][0] = rho1 - sum1;
-    f[1][0] = rho2 - sum2;
+    for (int i = 2; i < 19; ++i) sum = add2(sum, f[i]);
+    f[0] = sub2(rho, sum);
 }
 
 // ---------------------------------------------------------------------------
@@ -359,75 +376,80 @@ __device__ __forceinline__ void collide(C f[2][19], C rho1, C rho2, C inv_rho, c
 template <typename TS, int P>
 __global__ void __launch_bounds__(256) k_dens(DevState s)
 {
-    using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= s.n_fluid) return;
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
-    C f[2][19];
     const Nbr b = make_nbr(fl, s);
+    C2 f[19];
     load_pops<TS, P>(f, n, pv, fl, b, s);
-    C2 q;
-    q.x = sum19<C>(f[0]);
-    q.y = sum19<C>(f[1]);
-    reinterpret_cast<C2 *>(s.psi)[pv] = q;
+    reinterpret_cast<C2 *>(s.psi)[pv] = sum19(f);
 }
 
-// Eq. 15 at every wall voxel: rho-tilde^sigma = chi^sigma * (sum of w_i rho^sigma
+// Eq. 15 at one wall voxel: rho-tilde^sigma = chi^sigma * (sum of w_i rho^sigma
 // over in-domain fluid neighbours) / (sum of those w_i), chi = 1 +/- xi.
-template <typename TS>
-__global__ void __launch_bounds__(256) k_wall(DevState s)
+template <typename TS, bool L2ONLY>
+__device__ __forceinline__ void wall_node(int w, const DevState &s, void *psi_out)
 {
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= s.n_wall) return;
+    C2 *psi = reinterpret_cast<C2 *>(psi_out);
     const uint32_t pv = s.wpvox[w];
     const uint32_t mask = s.wmask[w];
-    const uint32_t fl = mask >> kWallFaceShift;
-    C2 *psi = reinterpret_cast<C2 *>(s.psi);
-    const Nbr b = make_nbr(fl, s);
-    C s1 = 0, s2 = 0;
+    const Nbr b = make_nbr(mask >> kWallFaceShift, s);
+    C2 acc = mk2(C(0), C(0));
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
         if (mask & (1u << j)) {
-            const C2 q = psi[(int)pv + nb_off(j, b)];
-            s1 += wgt<C>(j) * q.x;
-            s2 += wgt<C>(j) * q.y;
+            const C2 *q = psi + ((int)pv + nb_off(j, b));
+            acc = fma2(bc2<C2>(wgt<C>(j)), L2ONLY ? __ldcg(q) : *q, acc);
         }
     }
     const C inv = reinterpret_cast<const C *>(s.winv)[w];
     const C xi = reinterpret_cast<const C *>(s.wxi)[w];
-    C2 q;
-    q.x = (C(1) + xi) * s1 * inv;
-    q.y = (C(1) - xi) * s2 * inv;
-    psi[pv] = q;
+    psi[pv] = mul2(acc, mk2((C(1) + xi) * inv, (C(1) - xi) * inv));
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(256) k_wall(DevState s)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= s.n_wall) return;
+    wall_node<TS, false>(w, s, s.psi);
+}
+
+// F: the fused force / collision / streaming update of one node.
+template <typename TS, int P>
+__device__ __forceinline__ void fused_node(int n, const DevState &s)
+{
+    using C = typename Traits<TS>::C;
+    using C2 = typename Traits<TS>::C2;
+    const uint32_t pv = s.pvox[n];
+    const uint32_t fl = s.nflags[n];
+    const Nbr b = make_nbr(fl, s);
+    C2 f[19];
+    load_pops<TS, P>(f, n, pv, fl, b, s);
+    const C2 rho = sum19(f);
+    C2 F[3];
+    C u[3], inv_rho;
+    forces<TS>(rho, pv, fl, b, s, F);
+    mix_velocity<C, C2>(f, rho, F, s, inv_rho, u);
+    collide<C, C2>(f, rho, inv_rho, u, F, s);
+    store_pops<TS, P>(f, n, pv, fl, b, s);
 }
 
 template <typename TS, int P>
 __global__ void __launch_bounds__(256, 3) k_fused(DevState s)
 {
-    using C = typename Traits<TS>::C;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= s.n_fluid) return;
-    const uint32_t pv = s.pvox[n];
-    const uint32_t fl = s.nflags[n];
-    C f[2][19];
-    const Nbr b = make_nbr(fl, s);
-    load_pops<TS, P>(f, n, pv, fl, b, s);
-    const C rho1 = sum19<C>(f[0]);
-    const C rho2 = sum19<C>(f[1]);
-    C F1[3], F2[3], u[3], inv_rho;
-    forces<TS>(rho1, rho2, pv, fl, b, s, F1, F2);
-    mix_velocity<C>(f, rho1, rho2, F1, F2, s, inv_rho, u);
-    collide<C>(f, rho1, rho2, inv_rho, u, F1, F2, s);
-    store_pops<TS, P>(f, n, pv, fl, b, s);
+    fused_node<TS, P>(n, s);
 }
 
-// Open planes, run after a step for the parity PN of the step that reads next:
-// the prescribed component (1 at the inlet, 2 at the outlet) gets all 19
-// populations by non-equilibrium extrapolation from the first interior node,
+// Open planes, for the parity PN of the step that reads next: the prescribed
+// component (1 at the inlet, 2 at the outlet) gets all 19 populations by
+// non-equilibrium extrapolation from the first interior node,
 // f_i(xb) = f^eq_i(rho_b, u) + f_i(xi) - f^eq_i(rho(xi), u) with u the
 // barycentric velocity of xi; the other component's missing populations get
 // their initial values back (Section 2).
@@ -435,47 +457,52 @@ template <typename TS, int PN, bool L2ONLY>
 __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb, uint32_t flb, const DevState &s)
 {
     using C = typename Traits<TS>::C;
+    using C2 = typename Traits<TS>::C2;
+    using S2 = typename Traits<TS>::S2;
     const uint32_t pvi = plane == 0 ? pvb + s.sxy : pvb - s.sxy;
     const int ni = s.cidx[pvi];
     const uint32_t fli = s.nflags[ni];
     const Nbr bi = make_nbr(fli, s);
     const Nbr bb = make_nbr(flb, s);
-    C fi[2][19];
+    C2 fi[19];
     load_pops<TS, PN, L2ONLY>(fi, ni, pvi, fli, bi, s);
-    const C r1 = sum19<C>(fi[0]);
-    const C r2 = sum19<C>(fi[1]);
+    const C2 r = sum19(fi);
     C m[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
-        const C tt = fi[0][i] + fi[1][i];
+        const C tt = fi[i].x + fi[i].y;
         if (ex(i)) m[0] += ex(i) * tt;
         if (ey(i)) m[1] += ey(i) * tt;
         if (ez(i)) m[2] += ez(i) * tt;
     }
-    const C ir = C(1) / (r1 + r2);
+    const C ir = C(1) / (r.x + r.y);
     const C u[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
     const C usq = C(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
     const C rb = (C)(plane == 0 ? s.rho_in1 : s.rho_out2);
-    const C rin = plane == 0 ? r1 : r2;
-    TS *A = reinterpret_cast<TS *>(s.f);
-    const int pc = plane;  // prescribed component index
+    const C rin = plane == 0 ? r.x : r.y;
+    const int pc = plane;  // prescribed component
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         const C eu = ex(i) * u[0] + ey(i) * u[1] + ez(i) * u[2];
         const C base = C(1) + C(3) * eu + C(4.5) * eu * eu - usq;
-        const C fin = plane == 0 ? fi[0][i] : fi[1][i];
+        const C fin = plane == 0 ? fi[i].x : fi[i].y;
         const C v = wgt<C>(i) * rb * base + fin - wgt<C>(i) * rin * base;
-        if (i == 0)
-            Traits<TS>::store(A + (long long)pc * 19 * s.npad + nb, v, ref_of<TS>(s, pc, 0));
-        else
-            Traits<TS>::store(cell<TS>(s, pc, slot_of<PN>(opp(i), nb, pvb, flb, bb, s)), v, ref_of<TS>(s, pc, i));
+        if (i == 0) {
+            C2 rv = ld_rest<TS, L2ONLY>(s, nb);
+            if (pc == 0) rv.x = v; else rv.y = v;
+            st_rest<TS>(s, nb, rv);
+        } else {
+            S2 *q = slot_ptr<TS, PN>(opp(i), nb, pvb, flb, bb, s);
+            Traits<TS>::store1(q, pc, v, pc == 0 ? ref_of<TS>(s, i).x : ref_of<TS>(s, i).y);
+        }
     }
     const int qc = 1 - pc;
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
         const int i = miss_dir(plane, k);
         const C v = (C)s.frozen[(long long)(plane * 5 + k) * s.nxy + p];
-        Traits<TS>::store(cell<TS>(s, qc, slot_of<PN>(opp(i), nb, pvb, flb, bb, s)), v, ref_of<TS>(s, qc, i));
+        S2 *q = slot_ptr<TS, PN>(opp(i), nb, pvb, flb, bb, s);
+        Traits<TS>::store1(q, qc, v, qc == 0 ? ref_of<TS>(s, i).x : ref_of<TS>(s, i).y);
     }
 }
 
@@ -493,54 +520,56 @@ __global__ void __launch_bounds__(128) k_plane(DevState s)
 }
 
 // ---------------------------------------------------------------------------
-// State transfer and diagnostics
+// State transfer and diagnostics.  Host-side population arrays are
+// [sigma][i][v] doubles over the dense grid.
 
 template <typename TS>
 __global__ void k_init_eq(DevState s, const double *rho)
 {
     using C = typename Traits<TS>::C;
+    using C2 = typename Traits<TS>::C2;
+    using S2 = typename Traits<TS>::S2;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= s.n_fluid) return;
     const uint32_t pv = s.pvox[n];
-    TS *A = reinterpret_cast<TS *>(s.f);
+    const C2 r = mk2((C)rho[pv], (C)rho[s.nv + pv]);
+    st_rest<TS>(s, n, mul2(bc2<C2>(wgt<C>(0)), r));
+    S2 *M = reinterpret_cast<S2 *>(s.f);
 #pragma unroll
-    for (int sg = 0; sg < 2; ++sg) {
-        const C r = (C)rho[(long long)sg * s.nv + pv];
-#pragma unroll
-        for (int i = 0; i < 19; ++i)
-            Traits<TS>::store(A + ((long long)sg * 19 + i) * s.npad + n, wgt<C>(i) * r, ref_of<TS>(s, sg, i));
-    }
+    for (int i = 1; i < 19; ++i) Traits<TS>::store(M + (long long)(i - 1) * s.npad + n, mul2(bc2<C2>(wgt<C>(i)), r), ref_of<TS>(s, i));
 }
 
 template <typename TS>
 __global__ void k_scatter(DevState s, const double *f)
 {
     using C = typename Traits<TS>::C;
+    using S2 = typename Traits<TS>::S2;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= s.n_fluid) return;
-    const uint32_t pv = s.pvox[n];
-    TS *A = reinterpret_cast<TS *>(s.f);
-    for (int k = 0; k < 38; ++k) {
-        const int sg = k / 19, i = k % 19;
-        Traits<TS>::store(A + (long long)k * s.npad + n, (C)f[(long long)k * s.nv + pv], ref_of<TS>(s, sg, i));
-    }
+    const long long pv = s.pvox[n];
+    st_rest<TS>(s, n, mk2((C)f[pv], (C)f[19 * s.nv + pv]));
+    S2 *M = reinterpret_cast<S2 *>(s.f);
+    for (int i = 1; i < 19; ++i)
+        Traits<TS>::store(M + (long long)(i - 1) * s.npad + n, mk2((C)f[i * s.nv + pv], (C)f[(19 + i) * s.nv + pv]),
+                          ref_of<TS>(s, i));
 }
 
 template <typename TS, int P>
 __global__ void k_gather(DevState s, double *out)
 {
-    using C = typename Traits<TS>::C;
+    using C2 = typename Traits<TS>::C2;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= s.n_fluid) return;
     const uint32_t pv = s.pvox[n];
-    C f[2][19];
     const uint32_t fl = s.nflags[n];
     const Nbr b = make_nbr(fl, s);
+    C2 f[19];
     load_pops<TS, P>(f, n, pv, fl, b, s);
 #pragma unroll
-    for (int sg = 0; sg < 2; ++sg)
-#pragma unroll
-        for (int i = 0; i < 19; ++i) out[((long long)sg * 19 + i) * s.nv + pv] = (double)f[sg][i];
+    for (int i = 0; i < 19; ++i) {
+        out[(long long)i * s.nv + pv] = (double)f[i].x;
+        out[(long long)(19 + i) * s.nv + pv] = (double)f[i].y;
+    }
 }
 
 // Frozen values: the initial populations of the non-prescribed component in
@@ -548,7 +577,8 @@ __global__ void k_gather(DevState s, double *out)
 template <typename TS>
 __global__ void k_capture_frozen(DevState s, double *frozen)
 {
-    using C = typename Traits<TS>::C;
+    using C2 = typename Traits<TS>::C2;
+    using S2 = typename Traits<TS>::S2;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= 2 * s.nxy) return;
     const int plane = t >= s.nxy ? 1 : 0;
@@ -556,11 +586,14 @@ __global__ void k_capture_frozen(DevState s, double *frozen)
     const uint32_t pvb = plane == 0 ? (uint32_t)p : (uint32_t)(p + (s.nz - 1) * s.sxy);
     const int nb = s.cidx[pvb];
     const int qc = 1 - plane;
-    const TS *A = reinterpret_cast<const TS *>(s.f);
+    const S2 *M = reinterpret_cast<const S2 *>(s.f);
     for (int k = 0; k < 5; ++k) {
         const int i = miss_dir(plane, k);
         double v = 0;
-        if (nb >= 0) v = (double)Traits<TS>::load(A + ((long long)qc * 19 + i) * s.npad + nb, ref_of<TS>(s, qc, i));
+        if (nb >= 0) {
+            const C2 q = Traits<TS>::load(M + (long long)(i - 1) * s.npad + nb, ref_of<TS>(s, i));
+            v = (double)(qc == 0 ? q.x : q.y);
+        }
         frozen[(long long)(plane * 5 + k) * s.nxy + p] = v;
     }
 }
@@ -569,25 +602,26 @@ template <typename TS, int P>
 __global__ void k_fields(DevState s, double *out)
 {
     using C = typename Traits<TS>::C;
+    using C2 = typename Traits<TS>::C2;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= s.n_fluid) return;
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
-    C f[2][19];
     const Nbr b = make_nbr(fl, s);
+    C2 f[19];
     load_pops<TS, P>(f, n, pv, fl, b, s);
-    const C rho1 = sum19<C>(f[0]);
-    const C rho2 = sum19<C>(f[1]);
-    C F1[3], F2[3], u[3], inv_rho;
-    forces<TS>(rho1, rho2, pv, fl, b, s, F1, F2);
-    mix_velocity<C>(f, rho1, rho2, F1, F2, s, inv_rho, u);
+    const C2 rho = sum19(f);
+    C2 F[3];
+    C u[3], inv_rho;
+    forces<TS>(rho, pv, fl, b, s, F);
+    mix_velocity<C, C2>(f, rho, F, s, inv_rho, u);
     const C cs2 = C(1) / C(3);
-    out[0 * s.nv + pv] = (double)rho1;
-    out[1 * s.nv + pv] = (double)rho2;
+    out[0 * s.nv + pv] = (double)rho.x;
+    out[1 * s.nv + pv] = (double)rho.y;
     out[2 * s.nv + pv] = (double)u[0];
     out[3 * s.nv + pv] = (double)u[1];
     out[4 * s.nv + pv] = (double)u[2];
-    out[5 * s.nv + pv] = (double)(cs2 * (rho1 + rho2) + cs2 * (C)s.G * rho1 * rho2);
+    out[5 * s.nv + pv] = (double)(cs2 * (rho.x + rho.y) + cs2 * (C)s.G * rho.x * rho.y);
 }
 
 // FP64 reduction of the densities in psi (warp shuffle -> block -> partials).

@@ -90,32 +90,11 @@ __device__ __forceinline__ bool wait_upto(const int *flags, unsigned long long *
     return false;
 }
 
-// F: the fused force / collision / streaming update of one node (the body of
-// k_fused).
-template <typename TS, int P>
-__device__ __forceinline__ void fused_node(int n, const DevState &s)
-{
-    using C = typename Traits<TS>::C;
-    const uint32_t pv = s.pvox[n];
-    const uint32_t fl = s.nflags[n];
-    const Nbr b = make_nbr(fl, s);
-    C f[2][19];
-    load_pops<TS, P>(f, n, pv, fl, b, s);
-    const C rho1 = sum19<C>(f[0]);
-    const C rho2 = sum19<C>(f[1]);
-    C F1[3], F2[3], u[3], inv_rho;
-    forces<TS>(rho1, rho2, pv, fl, b, s, F1, F2);
-    mix_velocity<C>(f, rho1, rho2, F1, F2, s, inv_rho, u);
-    collide<C>(f, rho1, rho2, inv_rho, u, F1, F2, s);
-    store_pops<TS, P>(f, n, pv, fl, b, s);
-}
-
-// D: open-plane extrapolation (plane nodes) then the density of one node at
-// the parity PN of the next step, into psi_next.
+// D: open-plane extrapolation (plane nodes) then the density pair of one node
+// at the parity PN of the next step, into psi_next.
 template <typename TS, int PN>
 __device__ __forceinline__ void dens_node(int n, const DevState &s, void *psi_next)
 {
-    using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
@@ -125,39 +104,9 @@ __device__ __forceinline__ void dens_node(int n, const DevState &s, void *psi_ne
         neem_node<TS, PN, true>(plane, p, n, pv, fl, s);
     }
     const Nbr b = make_nbr(fl, s);
-    C f[2][19];
+    C2 f[19];
     load_pops<TS, PN, true>(f, n, pv, fl, b, s);
-    C2 q;
-    q.x = sum19<C>(f[0]);
-    q.y = sum19<C>(f[1]);
-    reinterpret_cast<C2 *>(psi_next)[pv] = q;
-}
-
-// W: Eq. 15 at one wall voxel from the next-step fluid densities.
-template <typename TS>
-__device__ __forceinline__ void wall_node(int w, const DevState &s, void *psi_next)
-{
-    using C = typename Traits<TS>::C;
-    using C2 = typename Traits<TS>::C2;
-    C2 *psi = reinterpret_cast<C2 *>(psi_next);
-    const uint32_t pv = s.wpvox[w];
-    const uint32_t mask = s.wmask[w];
-    const Nbr b = make_nbr(mask >> kWallFaceShift, s);
-    C s1 = 0, s2 = 0;
-#pragma unroll
-    for (int j = 1; j < 19; ++j) {
-        if (mask & (1u << j)) {
-            const C2 q = __ldcg(psi + ((int)pv + nb_off(j, b)));
-            s1 += wgt<C>(j) * q.x;
-            s2 += wgt<C>(j) * q.y;
-        }
-    }
-    const C inv = reinterpret_cast<const C *>(s.winv)[w];
-    const C xi = reinterpret_cast<const C *>(s.wxi)[w];
-    C2 q;
-    q.x = (C(1) + xi) * s1 * inv;
-    q.y = (C(1) - xi) * s2 * inv;
-    psi[pv] = q;
+    reinterpret_cast<C2 *>(psi_next)[pv] = sum19(f);
 }
 
 // Resident blocks per SM the register budget is sized for.
@@ -196,7 +145,8 @@ __global__ void __launch_bounds__(kChunk, PipeOcc<TS>::blocks) k_pipe(DevState s
         const int cw = k - ps.lag_w;
         if (cw >= 0 && cw < ps.n_chunks) {
             if (!wait_upto(ps.flag_d, ps.front + 1, ps.dep_d[cw].y, ps.epoch, ps, sh_w)) return;
-            for (int w = ps.wstart[cw] + threadIdx.x; w < ps.wstart[cw + 1]; w += kChunk) wall_node<TS>(w, s, ps.psi_next);
+            for (int w = ps.wstart[cw] + threadIdx.x; w < ps.wstart[cw + 1]; w += kChunk)
+                wall_node<TS, true>(w, s, ps.psi_next);
         }
         __syncthreads();  // sh_k is rewritten at the top
     }

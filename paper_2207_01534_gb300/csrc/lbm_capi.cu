@@ -182,7 +182,7 @@ void run_reduce(lbm_ctx *c)
 {
     dispatch(c, [&](auto tag) {
         using TS = decltype(tag);
-        Ops<TS>::dens(c->s, (int)(c->step & 1), c->stream);
+        Ops<TS>::dens(c->s, (int)(c->step & 1), c->step > 0, c->stream);
         Ops<TS>::wall(c->s, c->stream);
         Ops<TS>::reduce(c->s, c->d_partials, kReduceBlocks, c->d_red, c->stream);
     });
@@ -210,9 +210,6 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
     cudaStream_t st = c->stream;
     if (c->kernel == LBM_KERNEL_FUSED) {
         PipeState &ps = c->ps;
-        // every launch takes `tickets` work tickets plus one final, failing
-        // claim per block, so the counter advances by tickets + grid
-        ps.base = (unsigned long long)c->pipe_launches * (unsigned long long)(ps.tickets + c->pipe_grid);
         ps.epoch = (int)(c->pipe_launches + 1);
         ps.psi_next = c->psi_alt;
         dispatch(c, [&](auto tag) {
@@ -230,16 +227,15 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
     dispatch(c, [&](auto tag) {
         using TS = decltype(tag);
         if (ev) cudaEventRecord(ev[0], st);
-        Ops<TS>::dens(c->s, par, st);
+        Ops<TS>::dens(c->s, par, c->step > 0, st);
         if (ev) cudaEventRecord(ev[1], st);
         Ops<TS>::wall(c->s, st);
         if (ev) cudaEventRecord(ev[2], st);
         Ops<TS>::fused(c->s, par, st);
         if (ev) cudaEventRecord(ev[3], st);
-        Ops<TS>::plane(c->s, 1 - par, st);
         if (ev) cudaEventRecord(ev[4], st);
     });
-    c->launches += 2 + (c->s.n_wall > 0 ? 1 : 0) + (c->s.open_z ? 1 : 0);
+    c->launches += 2 + (c->s.n_wall > 0 ? 1 : 0);
     }
     c->step++;
     if (c->p.reduce_every > 0 && c->step % c->p.reduce_every == 0) {
@@ -503,33 +499,16 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
             }
         }
         wst[(size_t)NC] = (int)wpvox.size();
-        int reach_f = 0, reach_d = 0;
-        for (int64_t ch = 0; ch < NC; ++ch) {
-            reach_f = std::max(reach_f, dep_f[(size_t)ch].y - (int)ch);
-            if (dep_d[(size_t)ch].y >= dep_d[(size_t)ch].x) reach_d = std::max(reach_d, dep_d[(size_t)ch].y - (int)ch);
-        }
-        // Lags beyond the bare dependency reach by about the number of blocks
-        // in flight, so that a D or W phase rarely finds its inputs still
-        // being computed (the re-read window stays a few tens of MB of L2).
-        int sms = 0, per_sm = 0;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
-        dispatch(c, [&](auto tag) { per_sm = Ops<decltype(tag)>::pipe_blocks_per_sm(); });
-        const int resident = std::max(1, per_sm) * std::max(1, sms);
-        int slack = 2 * resident;
-        if (const char *e = std::getenv("LBM_PIPE_SLACK")) slack = std::max(0, std::atoi(e));
         PipeState &ps = c->ps;
         ps.n_chunks = (int)NC;
-        ps.lag_d = reach_f + 1 + slack;
-        ps.lag_w = ps.lag_d + reach_d + 1 + slack / 2;
-        ps.tickets = ps.n_chunks + ps.lag_w;
         ps.flag_f = (int *)A((size_t)NC * 4);
         ps.flag_d = (int *)A((size_t)NC * 4);
-        ps.dep_f = (const int2 *)A((size_t)NC * 8);
-        ps.dep_d = (const int2 *)A((size_t)NC * 8);
+        ps.need_f = (const int *)A((size_t)NC * 4);
+        ps.need_d = (const int *)A((size_t)NC * 4);
         ps.wstart = (const int *)A((size_t)(NC + 1) * 4);
-        ps.counter = (unsigned long long *)A(8);
+        ps.ctr = (unsigned long long *)A(48 * 8);    // three counters, 128 bytes apart
+        ps.front = (unsigned long long *)A(32 * 8);  // two frontiers, 128 bytes apart
         ps.abort = (int *)A(4);
-        ps.front = (unsigned long long *)A(16);
         c->psi_alt = A((size_t)nv * 2 * szc);
     }
     if (!ok) {
@@ -574,18 +553,23 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         const int64_t NC = ps.n_chunks;
         e = cudaMemset(ps.flag_f, 0, (size_t)NC * 4);
         if (e == cudaSuccess) e = cudaMemset(ps.flag_d, 0, (size_t)NC * 4);
-        if (e == cudaSuccess) e = cudaMemset(ps.counter, 0, 8);
+        if (e == cudaSuccess) e = cudaMemset(ps.ctr, 0, 48 * 8);
+        if (e == cudaSuccess) e = cudaMemset(ps.front, 0, 32 * 8);
         if (e == cudaSuccess) e = cudaMemset(ps.abort, 0, 4);
-        if (e == cudaSuccess) e = cudaMemset(ps.front, 0, 16);
         if (e == cudaSuccess) e = cudaMemset(c->psi_alt, 0, (size_t)nv * 2 * szc);
-        H2D((void *)ps.dep_f, dep_f.data(), (size_t)NC * 8);
-        H2D((void *)ps.dep_d, dep_d.data(), (size_t)NC * 8);
+        std::vector<int> nf((size_t)NC), nd((size_t)NC);
+        for (int64_t ch = 0; ch < NC; ++ch) {
+            nf[(size_t)ch] = dep_f[(size_t)ch].y;
+            nd[(size_t)ch] = dep_d[(size_t)ch].y >= dep_d[(size_t)ch].x ? dep_d[(size_t)ch].y : -1;
+        }
+        H2D((void *)ps.need_f, nf.data(), (size_t)NC * 4);
+        H2D((void *)ps.need_d, nd.data(), (size_t)NC * 4);
         H2D((void *)ps.wstart, wst.data(), (size_t)(NC + 1) * 4);
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
         int per_sm = 0;
         dispatch(c, [&](auto tag) { per_sm = Ops<decltype(tag)>::pipe_blocks_per_sm(); });
-        c->pipe_grid = std::max(1, std::min(ps.tickets, std::max(1, per_sm) * std::max(1, sms)));
+        c->pipe_grid = std::max(1, std::min(ps.n_chunks, std::max(1, per_sm) * std::max(1, sms)));
     }
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->h_flag, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) {
@@ -676,6 +660,10 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f)
     cudaError_t e = cudaMemsetAsync(d, 0, bytes, c->stream);
     dispatch(c, [&](auto tag) {
         using TS = decltype(tag);
+        // the open-plane extrapolation of the last step is applied lazily by
+        // the next density pass; apply it now (idempotent) so the returned
+        // state is the post-step state
+        if (c->step > 0) Ops<TS>::plane(c->s, (int)(c->step & 1), c->stream);
         Ops<TS>::gather(c->s, (int)(c->step & 1), d, c->stream);
     });
     c->launches += 1;
@@ -735,7 +723,7 @@ lbm_status lbm_read_fields(lbm_ctx *c, uint32_t mask, double *out, size_t n_per_
     const int par = (int)(c->step & 1);
     dispatch(c, [&](auto tag) {
         using TS = decltype(tag);
-        Ops<TS>::dens(c->s, par, c->stream);
+        Ops<TS>::dens(c->s, par, c->step > 0, c->stream);
         Ops<TS>::wall(c->s, c->stream);
         Ops<TS>::fields(c->s, par, d, c->stream);
     });

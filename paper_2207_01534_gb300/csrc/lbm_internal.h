@@ -55,38 +55,39 @@ struct DevState {
     int32_t velocity_shift;
 };
 
-// Single-pass schedule: one persistent launch per step works through tickets
-// k = 0 .. tickets-1 taken in order from a global counter.  Ticket k collides
-// and streams chunk k (F), then computes the next-step densities of chunk
-// k - lag_d (D, with the open-plane extrapolation for plane nodes), then the
-// wall densities of wall chunk k - lag_w (W).  A phase waits until the phases
-// it reads from have published their chunk flags; since every dependency
-// points to a lower ticket, and tickets are only taken by running blocks, the
-// waits always end (they are bounded anyway, see kPipeMaxPolls).
-constexpr int kChunk = 256;            // fluid nodes per chunk = threads per block
-constexpr int kPipeMaxPolls = 1 << 21; // polls of a flag range before giving up
+// Single-pass schedule: one persistent launch per step.  Its blocks claim
+// work chunks from three queues -- F (collide and stream chunk c), D (next-step
+// densities of chunk c, with the open-plane extrapolation) and W (wall
+// densities of wall chunk c) -- preferring W, then D, then F, and only claim a
+// D or W chunk once every chunk it reads from is done.  No block ever waits
+// inside a phase, so the launch cannot deadlock, and D runs right behind F
+// while the populations F wrote are still in L2.  Counters and completion
+// frontiers are tagged with the launch epoch, so nothing is reset between
+// launches.
+constexpr int kChunk = 256;             // fluid nodes per chunk = threads per block
+constexpr int kPipeMaxIdle = 1 << 22;   // idle polls of a block before it gives up
 
 struct PipeState {
     int *flag_f;                 // [n_chunks] epoch at which F of the chunk finished
     int *flag_d;                 // [n_chunks] epoch at which D of the chunk finished
-    unsigned long long *front;   // [2] per phase: (epoch << 32) | first chunk not known done
-    const int2 *dep_f;           // [n_chunks] chunk range whose F a chunk's D reads
-    const int2 *dep_d;           // [n_chunks] chunk range whose D a wall chunk's W reads
+    unsigned long long *ctr;     // claim counters F, D, W at [0], [16], [32]: (epoch << 32) | next chunk
+    unsigned long long *front;   // frontiers F, D at [0], [16]: (epoch << 32) | first chunk not known done
+    const int *need_f;           // [n_chunks] last F chunk that D of the chunk reads
+    const int *need_d;           // [n_chunks] last D chunk that W of the wall chunk reads (-1: none)
     const int *wstart;           // [n_chunks + 1] wall index range of each wall chunk
-    unsigned long long *counter; // ticket counter (never reset; see base)
-    unsigned long long base;     // counter value at the start of this launch
-    int *abort;                  // set when a wait gives up: every block stops
+    int *abort;                  // set when a block gives up: every block stops
     int *status;                 // host-mapped status word (bit 4: timeout)
     void *psi_next;              // densities of the next step (the other psi buffer)
     int epoch;                   // 1 + launches of this schedule so far
-    int n_chunks, lag_d, lag_w, tickets;
+    int n_chunks;
 };
 
 // Per-storage-type kernel launchers, explicitly instantiated in one
 // translation unit per storage type.
 template <typename TS>
 struct Ops {
-    static void dens(const DevState &s, int parity, cudaStream_t st);
+    // densities into psi; neem != 0 first applies the open-plane extrapolation
+    static void dens(const DevState &s, int parity, int neem, cudaStream_t st);
     static void wall(const DevState &s, cudaStream_t st);
     static void fused(const DevState &s, int parity, cudaStream_t st);
     static void plane(const DevState &s, int parity_next, cudaStream_t st);

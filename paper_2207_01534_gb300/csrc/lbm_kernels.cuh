@@ -373,14 +373,29 @@ __device__ __forceinline__ void collide(C2 f[19], C2 rho, C inv_rho, const C u[3
 // ---------------------------------------------------------------------------
 // Kernels of the split schedule
 
+// Density pass of the split schedule at parity P: plane nodes first apply the
+// open-plane extrapolation (idempotent: it only reads the interior node), then
+// every node sums its populations.  Nodes are taken in reverse order so the
+// pass starts on the lines the collide-stream kernel wrote last (still in L2).
+template <typename TS, int PN, bool L2ONLY>
+__device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb, uint32_t flb, const DevState &s);
+
+// neem = 0 skips the extrapolation (the state is an initial state that the
+// first step must see unchanged).
 template <typename TS, int P>
-__global__ void __launch_bounds__(256) k_dens(DevState s)
+__global__ void __launch_bounds__(256) k_dens(DevState s, int neem)
 {
     using C2 = typename Traits<TS>::C2;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= s.n_fluid) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= s.n_fluid) return;
+    const int n = s.n_fluid - 1 - t;
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
+    if (neem && (fl & (F_INLET | F_OUTLET))) {
+        const int plane = (fl & F_INLET) ? 0 : 1;
+        const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
+        neem_node<TS, P, false>(plane, p, n, pv, fl, s);
+    }
     const Nbr b = make_nbr(fl, s);
     C2 f[19];
     load_pops<TS, P>(f, n, pv, fl, b, s);

@@ -7,11 +7,11 @@ namespace lbm {
 static inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 template <typename TS>
-void Ops<TS>::dens(const DevState &s, int parity, cudaStream_t st)
+void Ops<TS>::dens(const DevState &s, int parity, int neem, cudaStream_t st)
 {
     if (s.n_fluid == 0) return;
-    if (parity) k_dens<TS, 1><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s);
-    else k_dens<TS, 0><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s);
+    if (parity) k_dens<TS, 1><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, neem && s.open_z);
+    else k_dens<TS, 0><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, neem && s.open_z);
 }
 
 template <typename TS>
@@ -84,7 +84,7 @@ void Ops<TS>::reduce(const DevState &s, double *partials, int nblocks, double *o
 template <typename TS>
 void Ops<TS>::pipe(const DevState &s, const PipeState &ps, int parity, int grid, cudaStream_t st)
 {
-    if (ps.tickets <= 0 || grid <= 0) return;
+    if (ps.n_chunks <= 0 || grid <= 0) return;
     if (parity) k_pipe<TS, 1><<<grid, kChunk, 0, st>>>(s, ps);
     else k_pipe<TS, 0><<<grid, kChunk, 0, st>>>(s, ps);
 }

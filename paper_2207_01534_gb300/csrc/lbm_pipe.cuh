@@ -1,16 +1,20 @@
 // lbm_pipe.cuh -- the single-pass schedule: one persistent launch per time
-// step that collides and streams every fluid node (F), computes the densities
-// of the next step (D, including the open-plane extrapolation) right behind
-// it while the freshly written populations are still in L2, and then the wall
-// virtual densities (W).  Populations are read from DRAM once per step.
+// step.  Blocks claim chunks of three kinds of work:
+//   F(c)  collide and stream the fluid nodes of chunk c,
+//   D(c)  next-step densities of chunk c (open-plane extrapolation first for
+//         plane nodes), read back while F's output is still in L2,
+//   W(c)  virtual densities of the walls between fluid chunks c and c+1.
+// D(c) may start once F is done for every chunk <= need_f[c]; W(c) once D is
+// done for every chunk <= need_d[c].  A block prefers a ready W, then a ready
+// D, then the next F; it never waits inside a phase.
 //
-// Ordering.  F(k) reads only data written by earlier launches.  D(c) reads
-// populations that F of neighbouring chunks wrote in this launch, so it waits
-// for their chunk flags (acquire) and reads with L2-only loads; F publishes its
-// flag after a block barrier and a device fence (release).  W(c) waits for D
-// the same way.  Every wait is bounded: after kPipeMaxPolls polls it sets the
-// abort word and a timeout bit in the host-mapped status word, and all blocks
-// stop at their next ticket.
+// Ordering.  A phase publishes its chunk flag after a block barrier and a
+// device-scope fence (release).  Completion frontiers ("every chunk below f
+// is done") advance in order through the flags, with a fence before each
+// update, and are read with acquire loads; data written in this launch is read
+// with L2-only loads.  Idle polling is bounded: after kPipeMaxIdle polls
+// without work a block sets the abort word and the timeout status bit, and
+// every block stops.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -24,22 +28,6 @@ __device__ __forceinline__ int ld_acquire(const int *p)
     return v;
 }
 
-__device__ __forceinline__ void st_release(int *p, int v)
-{
-    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-// Publish a phase of this block for chunk c: every thread's stores are
-// ordered before the flag by the barrier and the device-scope fence.
-__device__ __forceinline__ void publish(int *flags, int c, int epoch)
-{
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        st_release(flags + c, epoch);
-    }
-}
-
 __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long long *p)
 {
     unsigned long long v;
@@ -47,47 +35,74 @@ __device__ __forceinline__ unsigned long long ld_acquire64(const unsigned long l
     return v;
 }
 
-// Wait until every chunk <= hi of a phase has published `epoch` in flags.
-// front holds (epoch << 32) | f, meaning all chunks below f are known done in
-// that epoch; the fast path is one load of it.  Otherwise the whole block
-// scans flags[f .. hi] with independent acquire loads, advances front to the
-// first chunk not done (atomicMax: front only grows), and retries after a
-// short sleep.  Returns false after a timeout or an abort (block-uniform).
-__device__ __forceinline__ bool wait_upto(const int *flags, unsigned long long *front, int hi, int epoch,
-                                          const PipeState &ps, int *sh)
+__device__ __forceinline__ void st_release(int *p, int v)
 {
-    const unsigned long long tag = (unsigned long long)(unsigned)epoch << 32;
-    for (int it = 0; it < kPipeMaxPolls; ++it) {
-        if (threadIdx.x == 0) {
-            const unsigned long long f = ld_acquire64(front);
-            sh[0] = (f & 0xffffffff00000000ULL) == tag ? (int)(f & 0xffffffffULL) : 0;
-            sh[1] = 0x7fffffff;
-            sh[2] = *(volatile int *)ps.abort;
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr unsigned long long kLo = 0xffffffffULL;
+
+// Count part of an epoch-tagged word (0 when the word belongs to an older launch).
+__device__ __forceinline__ int tagged_count(unsigned long long v, unsigned long long tag)
+{
+    return (v & ~kLo) == tag ? (int)(v & kLo) : 0;
+}
+
+// Move a completion frontier forward over consecutive finished chunks.
+// Called by a whole warp: each round the 32 lanes check 32 flags at once and
+// lane 0 jumps the frontier over the finished prefix with one fenced CAS.
+__device__ __forceinline__ void advance_front(unsigned long long *front, const int *flags, unsigned long long tag,
+                                              int epoch, int n_chunks)
+{
+    const int lane = threadIdx.x & 31;
+    for (int round = 0; round < 16; ++round) {
+        const unsigned long long v = ld_acquire64(front);
+        const int f = tagged_count(v, tag);
+        if (f >= n_chunks) return;
+        const int m = f + lane;
+        const bool done = m >= n_chunks || ld_acquire(flags + m) >= epoch;
+        const unsigned ballot = __ballot_sync(0xffffffffu, done);
+        const int run = ballot == 0xffffffffu ? 32 : __ffs(~ballot) - 1;  // finished prefix length
+        if (run == 0) return;
+        int ok = 0;
+        if (lane == 0) {
+            __threadfence();
+            const int nf = min(f + run, n_chunks);
+            ok = atomicCAS(front, v, tag | (unsigned long long)nf) == v;
         }
-        __syncthreads();
-        const int lo = sh[0];
-        if (lo > hi) return true;
-        if (sh[2]) break;
-        int bad = 0x7fffffff;
-        for (int m = lo + threadIdx.x; m <= hi; m += blockDim.x)
-            if (ld_acquire(flags + m) < epoch) bad = min(bad, m);
-        if (bad != 0x7fffffff) atomicMin(&sh[1], bad);
-        __syncthreads();
-        const int first_bad = sh[1];
-        if (threadIdx.x == 0) atomicMax(front, tag | (unsigned)(first_bad == 0x7fffffff ? hi + 1 : first_bad));
-        if (first_bad == 0x7fffffff) {
-            __syncthreads();  // sh is rewritten by the next call
-            return true;
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+        if (ok && run < 32) return;  // stopped at an unfinished chunk
+    }
+}
+
+// Claim the next chunk of a queue if it exists and is ready (ready_upto >=
+// the chunk's need).  Returns the chunk or -1; *more says whether the queue
+// still has unclaimed chunks.
+__device__ __forceinline__ int try_claim(unsigned long long *ctr, unsigned long long tag, int n_chunks, const int *need,
+                                         int ready_upto, bool *more)
+{
+    *more = true;
+    for (int r = 0; r < 32; ++r) {  // retry when another block claimed first
+        const unsigned long long v = ld_acquire64(ctr);
+        const int k = tagged_count(v, tag);
+        if (k >= n_chunks) {
+            *more = false;
+            return -1;
         }
-        __nanosleep(128);
-        __syncthreads();
+        if (need && need[k] > ready_upto) return -1;
+        if (atomicCAS(ctr, v, tag | (unsigned long long)(k + 1)) == v) return k;
     }
-    if (threadIdx.x == 0) {
-        atomicExch(ps.abort, 1);
-        atomicOr(ps.status, 4);
-    }
+    return -1;
+}
+
+// Publish a phase of this block for chunk c.
+__device__ __forceinline__ void publish(int *flags, int c, int epoch)
+{
     __syncthreads();
-    return false;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        st_release(flags + c, epoch);
+    }
 }
 
 // D: open-plane extrapolation (plane nodes) then the density pair of one node
@@ -119,36 +134,76 @@ struct PipeOcc<double> {
     static constexpr int blocks = 2;
 };
 
+enum : int { kJobNone = 0, kJobF = 1, kJobD = 2, kJobW = 3, kJobExit = 4 };
+
 template <typename TS, int P>
 __global__ void __launch_bounds__(kChunk, PipeOcc<TS>::blocks) k_pipe(DevState s, PipeState ps)
 {
-    __shared__ int sh_k;
-    __shared__ int sh_w[3];
+    __shared__ int sh_job, sh_idx;
+    const unsigned long long tag = (unsigned long long)(unsigned)ps.epoch << 32;
+    unsigned long long *ctr_f = ps.ctr, *ctr_d = ps.ctr + 16, *ctr_w = ps.ctr + 32;  // separate 128-byte lines
+    unsigned long long *front_f = ps.front, *front_d = ps.front + 16;
+    int idle = 0, backoff = 64;
     for (;;) {
-        if (threadIdx.x == 0)
-            sh_k = *(volatile int *)ps.abort ? ps.tickets : (int)(atomicAdd(ps.counter, 1ULL) - ps.base);
+        if (threadIdx.x == 0) {
+            int job = kJobNone, idx = -1;
+            if (*(volatile int *)ps.abort) {
+                job = kJobExit;
+            } else {
+                const int fd = tagged_count(ld_acquire64(front_d), tag);  // D done below fd
+                const int ff = tagged_count(ld_acquire64(front_f), tag);  // F done below ff
+                bool more_w, more_d, more_f;
+                idx = try_claim(ctr_w, tag, ps.n_chunks, ps.need_d, fd - 1, &more_w);
+                if (idx >= 0) {
+                    job = kJobW;
+                } else {
+                    idx = try_claim(ctr_d, tag, ps.n_chunks, ps.need_f, ff - 1, &more_d);
+                    if (idx >= 0) {
+                        job = kJobD;
+                    } else {
+                        idx = try_claim(ctr_f, tag, ps.n_chunks, nullptr, 0, &more_f);
+                        if (idx >= 0) job = kJobF;
+                        else if (!more_w && !more_d && !more_f) job = kJobExit;
+                    }
+                }
+            }
+            sh_job = job;
+            sh_idx = idx;
+        }
         __syncthreads();
-        const int k = sh_k;
-        if (k >= ps.tickets) return;  // the same value in every thread of the block
-        if (k < ps.n_chunks) {
-            const int n = k * kChunk + threadIdx.x;
+        const int job = sh_job, idx = sh_idx;
+        __syncthreads();
+        if (job == kJobExit) return;
+        if (job == kJobNone) {
+            // nothing ready yet: help the frontiers along, then back off
+            if (threadIdx.x < 32) {
+                advance_front(front_f, ps.flag_f, tag, ps.epoch, ps.n_chunks);
+                advance_front(front_d, ps.flag_d, tag, ps.epoch, ps.n_chunks);
+            }
+            if (threadIdx.x == 0 && ++idle > kPipeMaxIdle) {
+                atomicExch(ps.abort, 1);
+                atomicOr(ps.status, 4);
+            }
+            __nanosleep(backoff);
+            backoff = min(backoff * 2, 2048);
+            continue;
+        }
+        backoff = 64;
+        idle = 0;
+        if (job == kJobF) {
+            const int n = idx * kChunk + threadIdx.x;
             if (n < s.n_fluid) fused_node<TS, P>(n, s);
-            publish(ps.flag_f, k, ps.epoch);
-        }
-        const int c = k - ps.lag_d;
-        if (c >= 0 && c < ps.n_chunks) {
-            if (!wait_upto(ps.flag_f, ps.front, ps.dep_f[c].y, ps.epoch, ps, sh_w)) return;
-            const int n = c * kChunk + threadIdx.x;
+            publish(ps.flag_f, idx, ps.epoch);
+            if (threadIdx.x < 32) advance_front(front_f, ps.flag_f, tag, ps.epoch, ps.n_chunks);
+        } else if (job == kJobD) {
+            const int n = idx * kChunk + threadIdx.x;
             if (n < s.n_fluid) dens_node<TS, 1 - P>(n, s, ps.psi_next);
-            publish(ps.flag_d, c, ps.epoch);
-        }
-        const int cw = k - ps.lag_w;
-        if (cw >= 0 && cw < ps.n_chunks) {
-            if (!wait_upto(ps.flag_d, ps.front + 1, ps.dep_d[cw].y, ps.epoch, ps, sh_w)) return;
-            for (int w = ps.wstart[cw] + threadIdx.x; w < ps.wstart[cw + 1]; w += kChunk)
+            publish(ps.flag_d, idx, ps.epoch);
+            if (threadIdx.x < 32) advance_front(front_d, ps.flag_d, tag, ps.epoch, ps.n_chunks);
+        } else {
+            for (int w = ps.wstart[idx] + threadIdx.x; w < ps.wstart[idx + 1]; w += kChunk)
                 wall_node<TS, true>(w, s, ps.psi_next);
         }
-        __syncthreads();  // sh_k is rewritten at the top
     }
 }
 

@@ -501,13 +501,12 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         wst[(size_t)NC] = (int)wpvox.size();
         PipeState &ps = c->ps;
         ps.n_chunks = (int)NC;
-        ps.flag_f = (int *)A((size_t)NC * 4);
-        ps.flag_d = (int *)A((size_t)NC * 4);
         ps.need_f = (const int *)A((size_t)NC * 4);
         ps.need_d = (const int *)A((size_t)NC * 4);
         ps.wstart = (const int *)A((size_t)(NC + 1) * 4);
-        ps.ctr = (unsigned long long *)A(48 * 8);    // three counters, 128 bytes apart
-        ps.front = (unsigned long long *)A(32 * 8);  // two frontiers, 128 bytes apart
+        // round counters: at most NC rounds (grid >= 1), 128 bytes apart
+        ps.round_f = (unsigned long long *)A((size_t)NC * 8 * 16 * 8);
+        ps.round_d = (unsigned long long *)A((size_t)NC * 8 * 16 * 8);
         ps.abort = (int *)A(4);
         c->psi_alt = A((size_t)nv * 2 * szc);
     }
@@ -551,10 +550,8 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     if (e == cudaSuccess && c->ps.n_chunks > 0) {
         PipeState &ps = c->ps;
         const int64_t NC = ps.n_chunks;
-        e = cudaMemset(ps.flag_f, 0, (size_t)NC * 4);
-        if (e == cudaSuccess) e = cudaMemset(ps.flag_d, 0, (size_t)NC * 4);
-        if (e == cudaSuccess) e = cudaMemset(ps.ctr, 0, 48 * 8);
-        if (e == cudaSuccess) e = cudaMemset(ps.front, 0, 32 * 8);
+        e = cudaMemset(ps.round_f, 0, (size_t)NC * 8 * 16 * 8);
+        if (e == cudaSuccess) e = cudaMemset(ps.round_d, 0, (size_t)NC * 8 * 16 * 8);
         if (e == cudaSuccess) e = cudaMemset(ps.abort, 0, 4);
         if (e == cudaSuccess) e = cudaMemset(c->psi_alt, 0, (size_t)nv * 2 * szc);
         std::vector<int> nf((size_t)NC), nd((size_t)NC);
@@ -569,7 +566,21 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
         int per_sm = 0;
         dispatch(c, [&](auto tag) { per_sm = Ops<decltype(tag)>::pipe_blocks_per_sm(); });
+        // every block must be resident (cooperative launch); lags in rounds
+        // cover the dependency reach so that waits target earlier rounds
         c->pipe_grid = std::max(1, std::min(ps.n_chunks, std::max(1, per_sm) * std::max(1, sms)));
+        const int G = c->pipe_grid;
+        int reach_f = 0, reach_d = 0;
+        for (int64_t ch = 0; ch < NC; ++ch) {
+            reach_f = std::max(reach_f, nf[(size_t)ch] - (int)ch);
+            if (nd[(size_t)ch] >= 0) reach_d = std::max(reach_d, nd[(size_t)ch] - (int)ch);
+        }
+        int lag = 1 + (reach_f + G - 1) / G;
+        if (const char *ev = std::getenv("LBM_PIPE_LAG")) lag = std::max(1, std::atoi(ev));
+        ps.lag_d = lag;
+        ps.lag_w = ps.lag_d + 1 + (reach_d + G - 1) / G;
+        ps.n_rounds = (ps.n_chunks + G - 1) / G;
+        ps.rounds = ps.n_rounds + ps.lag_w;
     }
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->h_flag, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) {

@@ -55,23 +55,27 @@ struct DevState {
     int32_t velocity_shift;
 };
 
-// Single-pass schedule: one persistent launch per step.  Its blocks claim
-// work chunks from three queues -- F (collide and stream chunk c), D (next-step
-// densities of chunk c, with the open-plane extrapolation) and W (wall
-// densities of wall chunk c) -- preferring W, then D, then F, and only claim a
-// D or W chunk once every chunk it reads from is done.  No block ever waits
-// inside a phase, so the launch cannot deadlock, and D runs right behind F
-// while the populations F wrote are still in L2.  Counters and completion
-// frontiers are tagged with the launch epoch, so nothing is reset between
-// launches.
+// Single-pass schedule: one cooperative launch per step (all blocks
+// co-resident).  Chunks are dealt round-robin: in round r block b collides and
+// streams chunk r*G + b (F), computes the next-step densities of chunk
+// (r - lag_d)*G + b (D, with the open-plane extrapolation), and the wall
+// densities of wall chunk (r - lag_w)*G + b (W).  D waits for F of every chunk
+// up to need_f[c]; W for D up to need_d[c].  F never waits, and the lags make
+// every wait target a phase that is already done or running without waiting,
+// so the launch always finishes; waits are bounded anyway (kPipeMaxPolls).
+// Completion frontiers are tagged with the launch epoch, so nothing is reset
+// between launches.
 constexpr int kChunk = 256;             // fluid nodes per chunk = threads per block
-constexpr int kPipeMaxIdle = 1 << 22;   // idle polls of a block before it gives up
+constexpr int kPipeMaxPolls = 1 << 22;  // polls of a frontier before a block gives up
 
 struct PipeState {
-    int *flag_f;                 // [n_chunks] epoch at which F of the chunk finished
-    int *flag_d;                 // [n_chunks] epoch at which D of the chunk finished
-    unsigned long long *ctr;     // claim counters F, D, W at [0], [16], [32]: (epoch << 32) | next chunk
-    unsigned long long *front;   // frontiers F, D at [0], [16]: (epoch << 32) | first chunk not known done
+    // Completion counters per chunk round R (chunks R*G .. R*G+G-1), one per
+    // warp slot: warp w of every block adds 1 when its nodes of that round are
+    // done (or it has none), so in launch `epoch` a round is complete once all
+    // its counters reach epoch * G.  They only grow: nothing is reset between
+    // launches.
+    unsigned long long *round_f; // [n_rounds][8 warp slots] for F, at stride 16 (128-byte lines)
+    unsigned long long *round_d; // [n_rounds][8 warp slots] for D, at stride 16
     const int *need_f;           // [n_chunks] last F chunk that D of the chunk reads
     const int *need_d;           // [n_chunks] last D chunk that W of the wall chunk reads (-1: none)
     const int *wstart;           // [n_chunks + 1] wall index range of each wall chunk
@@ -79,7 +83,7 @@ struct PipeState {
     int *status;                 // host-mapped status word (bit 4: timeout)
     void *psi_next;              // densities of the next step (the other psi buffer)
     int epoch;                   // 1 + launches of this schedule so far
-    int n_chunks;
+    int n_chunks, n_rounds, lag_d, lag_w, rounds;
 };
 
 // Per-storage-type kernel launchers, explicitly instantiated in one

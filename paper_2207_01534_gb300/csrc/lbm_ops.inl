@@ -85,8 +85,11 @@ template <typename TS>
 void Ops<TS>::pipe(const DevState &s, const PipeState &ps, int parity, int grid, cudaStream_t st)
 {
     if (ps.n_chunks <= 0 || grid <= 0) return;
-    if (parity) k_pipe<TS, 1><<<grid, kChunk, 0, st>>>(s, ps);
-    else k_pipe<TS, 0><<<grid, kChunk, 0, st>>>(s, ps);
+    DevState a = s;
+    PipeState b = ps;
+    void *args[] = {&a, &b};
+    const void *fn = parity ? (const void *)k_pipe<TS, 1> : (const void *)k_pipe<TS, 0>;
+    cudaLaunchCooperativeKernel(fn, dim3(grid), dim3(kChunk), args, 0, st);
 }
 
 template <typename TS>

@@ -56,6 +56,7 @@ struct lbm_ctx {
     bool have_ev = false;
     // single-pass schedule
     PipeState ps{};
+    std::vector<uint8_t> solid_host;  // the mask, for host-side statistics
     void *psi_alt = nullptr;
     int pipe_grid = 0;
     int64_t pipe_launches = 0;
@@ -146,10 +147,37 @@ void dfree(lbm_ctx *c, void *ptr)
 template <class Fn>
 void dispatch(const lbm_ctx *c, Fn &&fn)
 {
-    if (c->storage == LBM_STORE_FP64)
-        fn(double{});
-    else
-        fn(float{});
+    switch (c->storage) {
+    case LBM_STORE_FP64: fn(double{}); break;
+    case LBM_STORE_FP16DEV: fn(__half{}); break;
+    case LBM_STORE_BF16DEV: fn(__nv_bfloat16{}); break;
+    default: fn(float{}); break;
+    }
+}
+
+bool is16(int storage) { return storage == LBM_STORE_FP16DEV || storage == LBM_STORE_BF16DEV; }
+
+// Reference densities of the 16-bit deviation storage: the parameters when
+// given, else the mean of each component over the fluid voxels of the state
+// being loaded.
+void choose_rho_ref(lbm_ctx *c, const double *r1, const double *r2, int64_t stride)
+{
+    if (!is16(c->storage) || c->p.rho_ref[0] != 0.0 || c->p.rho_ref[1] != 0.0) return;
+    double m[2] = {0, 0};
+    int64_t cnt = 0;
+    for (int64_t v = 0; v < c->nv; ++v) {
+        if (c->solid_host[(size_t)v]) continue;
+        double a = 0, b = 0;
+        for (int i = 0; i < (stride ? 19 : 1); ++i) {
+            a += r1[v + i * stride];
+            b += r2[v + i * stride];
+        }
+        m[0] += a;
+        m[1] += b;
+        ++cnt;
+    }
+    c->s.rref1 = cnt ? m[0] / (double)cnt : 0.0;
+    c->s.rref2 = cnt ? m[1] / (double)cnt : 0.0;
 }
 
 constexpr int kEx[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
@@ -290,8 +318,8 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     const bool open_z = g->open_axis == 2;
     if (open_z && (g->periodic[2] || nz < 3))
         return fail(nullptr, LBM_ERR_ARG, "the open axis must be non-periodic and at least 3 voxels long");
-    if (p->storage != LBM_STORE_FP32 && p->storage != LBM_STORE_FP64)
-        return fail(nullptr, LBM_ERR_UNSUPPORTED, "storage type not supported by this build");
+    if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16DEV)
+        return fail(nullptr, LBM_ERR_UNSUPPORTED, "unknown storage type");
     if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau must exceed 1/2");
     if (p->bc != LBM_BC_NEEM) return fail(nullptr, LBM_ERR_UNSUPPORTED, "only the NEEM boundary is supported");
     if (p->reduce_every < 0) return fail(nullptr, LBM_ERR_ARG, "reduce_every must be >= 0");
@@ -391,8 +419,8 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     c->storage = p->storage;
     c->kernel = p->kernel == LBM_KERNEL_FUSED ? LBM_KERNEL_FUSED : LBM_KERNEL_SPLIT;
 
-    const size_t sz = p->storage == LBM_STORE_FP64 ? 8 : 4;  // population storage bytes
-    const size_t szc = sz;                                     // compute-type bytes
+    const size_t sz = p->storage == LBM_STORE_FP64 ? 8 : (is16(p->storage) ? 2 : 4);  // stored element bytes
+    const size_t szc = p->storage == LBM_STORE_FP64 ? 8 : 4;                            // compute-type bytes
     const int64_t npad = ((N + 63) / 64) * 64 + 64;
     const int nxy = nx * ny;
     DevState &s = c->s;
@@ -417,8 +445,9 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     s.gz = p->body_force[2];
     s.rho_in1 = p->rho_in1;
     s.rho_out2 = p->rho_out2;
-    s.rref1 = 0;
-    s.rref2 = 0;
+    s.rref1 = p->rho_ref[0];
+    s.rref2 = p->rho_ref[1];
+    c->solid_host.assign(solid, solid + nv);
     s.velocity_shift = p->velocity_shift ? 1 : 0;
 
     bool ok = true;
@@ -612,6 +641,7 @@ void lbm_destroy(lbm_ctx *c)
 lbm_status lbm_init_densities(lbm_ctx *c, const double *rho1, const double *rho2)
 {
     if (!c || !rho1 || !rho2) return LBM_ERR_ARG;
+    choose_rho_ref(c, rho1, rho2, 0);
     const size_t bytes = (size_t)c->nv * 8;
     double *d = (double *)dalloc(c, 2 * bytes);
     if (!d) return fail(c, LBM_ERR_ALLOC, "temporary density buffer");
@@ -639,6 +669,7 @@ lbm_status lbm_init_densities(lbm_ctx *c, const double *rho1, const double *rho2
 lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
 {
     if (!c || !f) return LBM_ERR_ARG;
+    choose_rho_ref(c, f, f + 19 * c->nv, c->nv);
     const size_t bytes = (size_t)38 * c->nv * 8;
     double *d = (double *)dalloc(c, bytes);
     if (!d) return fail(c, LBM_ERR_ALLOC, "temporary population buffer");

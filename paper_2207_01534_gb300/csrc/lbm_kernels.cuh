@@ -125,6 +125,12 @@ struct Traits<float> {
     __device__ static __forceinline__ C2 load_cg(const S2 *p, C2) { return __ldcg(p); }
     __device__ static __forceinline__ void store(S2 *p, C2 v, C2) { *p = v; }
     __device__ static __forceinline__ void store1(S2 *p, int sg, C v, C) { (sg ? p->y : p->x) = v; }
+    __device__ static __forceinline__ S2 quant(C2 v, C2) { return v; }
+    __device__ static __forceinline__ C2 dequant(S2 q, C2) { return q; }
+    __device__ static __forceinline__ void store_q(S2 *p, S2 q) { *p = q; }
+    template <bool L2ONLY>
+    __device__ static __forceinline__ C2 load_dev(const S2 *p) { return L2ONLY ? __ldcg(p) : __ldg(p); }
+    __device__ static __forceinline__ C2 code_value(S2 q) { return q; }
 };
 
 template <>
@@ -138,7 +144,77 @@ struct Traits<double> {
     __device__ static __forceinline__ C2 load_cg(const S2 *p, C2) { return __ldcg(p); }
     __device__ static __forceinline__ void store(S2 *p, C2 v, C2) { *p = v; }
     __device__ static __forceinline__ void store1(S2 *p, int sg, C v, C) { (sg ? p->y : p->x) = v; }
+    __device__ static __forceinline__ S2 quant(C2 v, C2) { return v; }
+    __device__ static __forceinline__ C2 dequant(S2 q, C2) { return q; }
+    __device__ static __forceinline__ void store_q(S2 *p, S2 q) { *p = q; }
+    template <bool L2ONLY>
+    __device__ static __forceinline__ C2 load_dev(const S2 *p) { return L2ONLY ? __ldcg(p) : __ldg(p); }
+    __device__ static __forceinline__ C2 code_value(S2 q) { return q; }
 };
+
+// 16-bit storage: a moving population is kept as the FP16 / BF16 deviation
+// f_i - w_i rho_ref^sigma (one 4-byte pair for both components); arithmetic
+// is FP32 and the rest population stays an FP32 pair.
+template <typename H2, typename H1>
+struct Traits16 {
+    using C = float;
+    using C2 = float2;
+    using S2 = H2;
+    using R2 = float2;
+    static constexpr bool kDev = true;
+    __device__ static __forceinline__ C2 unpack(unsigned u)
+    {
+        H2 h;
+        memcpy(&h, &u, 4);
+        return to_float2(h);
+    }
+    __device__ static __forceinline__ float2 to_float2(__half2 h) { return __half22float2(h); }
+    __device__ static __forceinline__ float2 to_float2(__nv_bfloat162 h) { return __bfloat1622float2(h); }
+    __device__ static __forceinline__ void from_float2(float2 v, __half2 *h) { *h = __float22half2_rn(v); }
+    __device__ static __forceinline__ void from_float2(float2 v, __nv_bfloat162 *h) { *h = __float22bfloat162_rn(v); }
+    __device__ static __forceinline__ void from_float(float v, __half *h) { *h = __float2half_rn(v); }
+    __device__ static __forceinline__ void from_float(float v, __nv_bfloat16 *h) { *h = __float2bfloat16_rn(v); }
+    __device__ static __forceinline__ S2 quant(C2 v, C2 ref)
+    {
+        S2 h;
+        from_float2(make_float2(v.x - ref.x, v.y - ref.y), &h);
+        return h;
+    }
+    __device__ static __forceinline__ C2 dequant(S2 q, C2 ref)
+    {
+        const float2 d = to_float2(q);
+        return make_float2(ref.x + d.x, ref.y + d.y);
+    }
+    __device__ static __forceinline__ C2 load(const S2 *p, C2 ref)
+    {
+        const float2 d = unpack(__ldg(reinterpret_cast<const unsigned *>(p)));
+        return make_float2(ref.x + d.x, ref.y + d.y);
+    }
+    __device__ static __forceinline__ C2 load_cg(const S2 *p, C2 ref)
+    {
+        const float2 d = unpack(__ldcg(reinterpret_cast<const unsigned *>(p)));
+        return make_float2(ref.x + d.x, ref.y + d.y);
+    }
+    __device__ static __forceinline__ void store(S2 *p, C2 v, C2 ref) { *p = quant(v, ref); }
+    __device__ static __forceinline__ void store_q(S2 *p, S2 q) { *p = q; }
+    __device__ static __forceinline__ void store1(S2 *p, int sg, C v, C ref)
+    {
+        H1 *h = reinterpret_cast<H1 *>(p) + sg;
+        from_float(v - ref, h);
+    }
+    // the stored deviation itself, as FP32
+    template <bool L2ONLY>
+    __device__ static __forceinline__ C2 load_dev(const S2 *p)
+    {
+        return unpack(L2ONLY ? __ldcg(reinterpret_cast<const unsigned *>(p)) : __ldg(reinterpret_cast<const unsigned *>(p)));
+    }
+    __device__ static __forceinline__ C2 code_value(S2 q) { return to_float2(q); }
+};
+
+template <>
+struct Traits<__half> : Traits16<__half2, __half> {};
+template <>
+struct Traits<__nv_bfloat16> : Traits16<__nv_bfloat162, __nv_bfloat16> {};
 
 template <typename TS>
 __device__ __forceinline__ typename Traits<TS>::C2 ref_of(const DevState &s, int i)
@@ -148,18 +224,38 @@ __device__ __forceinline__ typename Traits<TS>::C2 ref_of(const DevState &s, int
     return mk2(wgt<C>(i) * (C)s.rref1, wgt<C>(i) * (C)s.rref2);
 }
 
-// Rest-population pair of node n (kept at compute precision: FP32 for the
-// 16-bit storage forms).
+// Rest-population pair of node n, kept at compute precision.  With deviation
+// storage the array holds f_0 - w_0 rho_ref (FP32); ld_rest returns f_0 and
+// ld_rest_dev the stored deviation.
 template <typename TS, bool L2ONLY>
-__device__ __forceinline__ typename Traits<TS>::C2 ld_rest(const DevState &s, int n)
+__device__ __forceinline__ typename Traits<TS>::C2 ld_rest_dev(const DevState &s, int n)
 {
     const typename Traits<TS>::R2 *R = reinterpret_cast<const typename Traits<TS>::R2 *>(s.rest);
     return L2ONLY ? __ldcg(R + n) : __ldg(R + n);
 }
+template <typename TS, bool L2ONLY>
+__device__ __forceinline__ typename Traits<TS>::C2 ld_rest(const DevState &s, int n)
+{
+    const typename Traits<TS>::C2 v = ld_rest_dev<TS, L2ONLY>(s, n);
+    return Traits<TS>::kDev ? add2(v, ref_of<TS>(s, 0)) : v;
+}
+template <typename TS>
+__device__ __forceinline__ void st_rest_dev(const DevState &s, int n, typename Traits<TS>::C2 v)
+{
+    reinterpret_cast<typename Traits<TS>::R2 *>(s.rest)[n] = v;
+}
 template <typename TS>
 __device__ __forceinline__ void st_rest(const DevState &s, int n, typename Traits<TS>::C2 v)
 {
-    reinterpret_cast<typename Traits<TS>::R2 *>(s.rest)[n] = v;
+    st_rest_dev<TS>(s, n, Traits<TS>::kDev ? sub2(v, ref_of<TS>(s, 0)) : v);
+}
+
+// Density pair from the mass accumulated by load_pops (see there).
+template <typename TS>
+__device__ __forceinline__ typename Traits<TS>::C2 density_of(typename Traits<TS>::C2 dm, const DevState &s)
+{
+    using C = typename Traits<TS>::C;
+    return Traits<TS>::kDev ? add2(dm, mk2((C)s.rref1, (C)s.rref2)) : dm;
 }
 
 // ---------------------------------------------------------------------------
@@ -229,41 +325,6 @@ __device__ __forceinline__ typename Traits<TS>::S2 *slot_ptr(int j, int n, uint3
     return reinterpret_cast<S2 *>(s.f) + slot_in_block<P>(j, n, pv, b, s);
 }
 
-// Post-stream population pairs f[i] of node n at parity P.  L2ONLY loads
-// bypass L1 (for data written earlier in the same launch).
-template <typename TS, int P, bool L2ONLY = false>
-__device__ __forceinline__ void load_pops(typename Traits<TS>::C2 f[19], int n, uint32_t pv, uint32_t fl,
-                                          const Nbr &b, const DevState &s)
-{
-    using S2 = typename Traits<TS>::S2;
-    const S2 *M = reinterpret_cast<const S2 *>(s.f);
-    const S2 *B = reinterpret_cast<const S2 *>(s.bc);
-    const bool plane = P == 1 && (fl & (F_INLET | F_OUTLET));
-    f[0] = ld_rest<TS, L2ONLY>(s, n);
-#pragma unroll
-    for (int j = 1; j < 19; ++j) {
-        const S2 *p = (ez(j) != 0 && plane && outside(j, fl)) ? B + bc_cell(j, pv, fl, s)
-                                                               : M + slot_in_block<P>(j, n, pv, b, s);
-        f[opp(j)] = L2ONLY ? Traits<TS>::load_cg(p, ref_of<TS>(s, j)) : Traits<TS>::load(p, ref_of<TS>(s, j));
-    }
-}
-
-// Post-collision population pairs f[i] of node n into their slots.
-template <typename TS, int P>
-__device__ __forceinline__ void store_pops(const typename Traits<TS>::C2 f[19], int n, uint32_t pv, uint32_t fl,
-                                           const Nbr &b, const DevState &s)
-{
-    using S2 = typename Traits<TS>::S2;
-    S2 *M = reinterpret_cast<S2 *>(s.f);
-    const bool plane = P == 1 && (fl & (F_INLET | F_OUTLET));
-    st_rest<TS>(s, n, f[0]);
-#pragma unroll
-    for (int j = 1; j < 19; ++j) {
-        if (ez(j) != 0 && plane && outside(j, fl)) continue;  // leaves the domain
-        Traits<TS>::store(M + slot_in_block<P>(j, n, pv, b, s), f[j], ref_of<TS>(s, j));
-    }
-}
-
 // rho^sigma = sum_i f_i^sigma (Eq. 3), in direction order for both components.
 template <typename C2>
 __device__ __forceinline__ C2 sum19(const C2 f[19])
@@ -272,6 +333,76 @@ __device__ __forceinline__ C2 sum19(const C2 f[19])
 #pragma unroll
     for (int i = 1; i < 19; ++i) r = add2(r, f[i]);
     return r;
+}
+
+// Post-stream population pairs f[i] of node n at parity P, and its mass dm:
+// the density pair sum_i f_i (direction order) for plain storage, or for
+// deviation storage the deviation mass (rest deviation + sum of the stored
+// deviations), so that mass bookkeeping never adds the large common offsets
+// w_i rho_ref (whose identical rounding at every node would bias it); the
+// density is then density_of(dm) = rho_ref + dm.  L2ONLY loads bypass L1 (for
+// data written earlier in the same launch).
+template <typename TS, int P, bool L2ONLY = false>
+__device__ __forceinline__ void load_pops(typename Traits<TS>::C2 f[19], typename Traits<TS>::C2 &dm, int n,
+                                          uint32_t pv, uint32_t fl, const Nbr &b, const DevState &s)
+{
+    using C2 = typename Traits<TS>::C2;
+    using S2 = typename Traits<TS>::S2;
+    const S2 *M = reinterpret_cast<const S2 *>(s.f);
+    const S2 *B = reinterpret_cast<const S2 *>(s.bc);
+    const bool plane = P == 1 && (fl & (F_INLET | F_OUTLET));
+    const C2 r0 = ld_rest_dev<TS, L2ONLY>(s, n);
+    if (Traits<TS>::kDev) {
+        dm = r0;
+        f[0] = add2(r0, ref_of<TS>(s, 0));
+    } else {
+        f[0] = r0;
+    }
+#pragma unroll
+    for (int j = 1; j < 19; ++j) {
+        const S2 *p = (ez(j) != 0 && plane && outside(j, fl)) ? B + bc_cell(j, pv, fl, s)
+                                                               : M + slot_in_block<P>(j, n, pv, b, s);
+        if (Traits<TS>::kDev) {
+            const C2 d = Traits<TS>::template load_dev<L2ONLY>(p);
+            dm = add2(dm, d);
+            f[opp(j)] = add2(d, ref_of<TS>(s, j));
+        } else {
+            f[opp(j)] = L2ONLY ? Traits<TS>::load_cg(p, ref_of<TS>(s, j)) : Traits<TS>::load(p, ref_of<TS>(s, j));
+        }
+    }
+    if (!Traits<TS>::kDev) dm = sum19(f);
+}
+
+// Post-collision population pairs f[i] of node n into their slots.  dm is the
+// node's mass from load_pops.  For deviation storage the moving populations
+// are quantised first and the rest deviation is dm minus the stored moving
+// deviations, so the stored mass equals the mass before collision exactly up
+// to FP32 rounding of deviation-sized terms; the codes are stored as computed
+// (never re-quantised).
+template <typename TS, int P>
+__device__ __forceinline__ void store_pops(typename Traits<TS>::C2 f[19], typename Traits<TS>::C2 dm, int n,
+                                           uint32_t pv, uint32_t fl, const Nbr &b, const DevState &s)
+{
+    using C2 = typename Traits<TS>::C2;
+    using S2 = typename Traits<TS>::S2;
+    S2 *M = reinterpret_cast<S2 *>(s.f);
+    const bool plane = P == 1 && (fl & (F_INLET | F_OUTLET));
+    S2 q[19];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) q[i] = Traits<TS>::quant(f[i], ref_of<TS>(s, i));
+    if (Traits<TS>::kDev) {
+        C2 sum = Traits<TS>::code_value(q[1]);
+#pragma unroll
+        for (int i = 2; i < 19; ++i) sum = add2(sum, Traits<TS>::code_value(q[i]));
+        st_rest_dev<TS>(s, n, sub2(dm, sum));
+    } else {
+        st_rest_dev<TS>(s, n, f[0]);
+    }
+#pragma unroll
+    for (int j = 1; j < 19; ++j) {
+        if (ez(j) != 0 && plane && outside(j, fl)) continue;  // leaves the domain
+        Traits<TS>::store_q(M + slot_in_block<P>(j, n, pv, b, s), q[j]);
+    }
 }
 
 // Force of Eqs. 10, 11, 13 for both components:
@@ -370,6 +501,16 @@ __device__ __forceinline__ void collide(C2 f[19], C2 rho, C inv_rho, const C u[3
     f[0] = sub2(rho, sum);
 }
 
+// Resident blocks per SM the register budget is sized for.
+template <typename TS>
+struct PipeOcc {
+    static constexpr int blocks = 3;
+};
+template <>
+struct PipeOcc<double> {
+    static constexpr int blocks = 2;
+};
+
 // ---------------------------------------------------------------------------
 // Kernels of the split schedule
 
@@ -397,9 +538,9 @@ __global__ void __launch_bounds__(256) k_dens(DevState s, int neem)
         neem_node<TS, P, false>(plane, p, n, pv, fl, s);
     }
     const Nbr b = make_nbr(fl, s);
-    C2 f[19];
-    load_pops<TS, P>(f, n, pv, fl, b, s);
-    reinterpret_cast<C2 *>(s.psi)[pv] = sum19(f);
+    C2 f[19], dm;
+    load_pops<TS, P>(f, dm, n, pv, fl, b, s);
+    reinterpret_cast<C2 *>(s.psi)[pv] = density_of<TS>(dm, s);
 }
 
 // Eq. 15 at one wall voxel: rho-tilde^sigma = chi^sigma * (sum of w_i rho^sigma
@@ -443,19 +584,19 @@ __device__ __forceinline__ void fused_node(int n, const DevState &s)
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
     const Nbr b = make_nbr(fl, s);
-    C2 f[19];
-    load_pops<TS, P>(f, n, pv, fl, b, s);
-    const C2 rho = sum19(f);
+    C2 f[19], dm;
+    load_pops<TS, P>(f, dm, n, pv, fl, b, s);
+    const C2 rho = density_of<TS>(dm, s);
     C2 F[3];
     C u[3], inv_rho;
     forces<TS>(rho, pv, fl, b, s, F);
     mix_velocity<C, C2>(f, rho, F, s, inv_rho, u);
     collide<C, C2>(f, rho, inv_rho, u, F, s);
-    store_pops<TS, P>(f, n, pv, fl, b, s);
+    store_pops<TS, P>(f, dm, n, pv, fl, b, s);
 }
 
 template <typename TS, int P>
-__global__ void __launch_bounds__(256, 3) k_fused(DevState s)
+__global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused(DevState s)
 {
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= s.n_fluid) return;
@@ -479,9 +620,9 @@ __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb
     const uint32_t fli = s.nflags[ni];
     const Nbr bi = make_nbr(fli, s);
     const Nbr bb = make_nbr(flb, s);
-    C2 fi[19];
-    load_pops<TS, PN, L2ONLY>(fi, ni, pvi, fli, bi, s);
-    const C2 r = sum19(fi);
+    C2 fi[19], dmi;
+    load_pops<TS, PN, L2ONLY>(fi, dmi, ni, pvi, fli, bi, s);
+    const C2 r = density_of<TS>(dmi, s);
     C m[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
@@ -578,8 +719,8 @@ __global__ void k_gather(DevState s, double *out)
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
     const Nbr b = make_nbr(fl, s);
-    C2 f[19];
-    load_pops<TS, P>(f, n, pv, fl, b, s);
+    C2 f[19], dm;
+    load_pops<TS, P>(f, dm, n, pv, fl, b, s);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
         out[(long long)i * s.nv + pv] = (double)f[i].x;
@@ -623,9 +764,9 @@ __global__ void k_fields(DevState s, double *out)
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
     const Nbr b = make_nbr(fl, s);
-    C2 f[19];
-    load_pops<TS, P>(f, n, pv, fl, b, s);
-    const C2 rho = sum19(f);
+    C2 f[19], dm;
+    load_pops<TS, P>(f, dm, n, pv, fl, b, s);
+    const C2 rho = density_of<TS>(dm, s);
     C2 F[3];
     C u[3], inv_rho;
     forces<TS>(rho, pv, fl, b, s, F);

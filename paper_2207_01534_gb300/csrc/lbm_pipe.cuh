@@ -88,20 +88,10 @@ __device__ __forceinline__ void dens_node(int n, const DevState &s, void *psi_ne
         neem_node<TS, PN, true>(plane, p, n, pv, fl, s);
     }
     const Nbr b = make_nbr(fl, s);
-    C2 f[19];
-    load_pops<TS, PN, true>(f, n, pv, fl, b, s);
-    reinterpret_cast<C2 *>(psi_next)[pv] = sum19(f);
+    C2 f[19], dm;
+    load_pops<TS, PN, true>(f, dm, n, pv, fl, b, s);
+    reinterpret_cast<C2 *>(psi_next)[pv] = density_of<TS>(dm, s);
 }
-
-// Resident blocks per SM the register budget is sized for.
-template <typename TS>
-struct PipeOcc {
-    static constexpr int blocks = 3;
-};
-template <>
-struct PipeOcc<double> {
-    static constexpr int blocks = 2;
-};
 
 template <typename TS, int P>
 __global__ void __launch_bounds__(kChunk, PipeOcc<TS>::blocks) k_pipe(DevState s, PipeState ps)

@@ -99,3 +99,18 @@ def duct_series_velocity(nxf, nyf, g, nu, nterms=101):
         coef = 4.0 * g / (nu * a * kn ** 3)
         u += coef * np.sin(kn * X) * (1.0 - np.cosh(kn * (Y - b / 2)) / np.cosh(kn * b / 2))
     return u
+
+
+def trapped_wetting_volume(f, solid, reservoir):
+    """Wetting-phase (component 2, rho2 > rho1) fluid nodes in 18-connected
+    clusters that do not reach the outlet reservoir (the last `reservoir`
+    z slices): the trapped volume of a drainage."""
+    from scipy import ndimage
+
+    water = (f["rho2"] > f["rho1"]) & (solid == 0)
+    lab, n = ndimage.label(water, structure=ndimage.generate_binary_structure(3, 2))
+    if n == 0:
+        return 0
+    outlet = set(np.unique(lab[-reservoir:][lab[-reservoir:] > 0]).tolist())
+    trapped = (lab > 0) & ~np.isin(lab, list(outlet))
+    return int(trapped.sum())

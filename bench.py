@@ -29,7 +29,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "MLUPS (2-component D3Q19)"
 UNIT = "MLUPS"
-ALGO_BYTES_FP32 = 2 * 19 * 4 * 2 + 4  # pops read + written, plus the node's voxel index
+# algorithmic bytes per fluid-node update: the 18 moving population pairs and
+# the rest pair, read once and written once, plus the node's voxel index
+ALGO_BYTES = {"fp32": 2 * (18 * 8 + 8) + 4, "fp64": 2 * (18 * 16 + 16) + 4,
+              "fp16dev": 2 * (18 * 4 + 8) + 4, "bf16dev": 2 * (18 * 4 + 8) + 4}
+DTYPE = {"fp32": "f32", "fp64": "f64", "fp16dev": "f32 (f16 storage)", "bf16dev": "f32 (bf16 storage)"}
 WORKLOAD = "drainage_pack_128"
 
 
@@ -186,7 +190,7 @@ def run_ours(args, rank, world):
     nvox = solid.size
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
-        lat = lbm.Lattice(solid, kernel=args.kernel, stream=stream.cuda_stream, **kw)
+        lat = lbm.Lattice(solid, kernel=args.kernel, storage=args.storage, stream=stream.cuda_stream, **kw)
         lat.init_densities(r1, r2)
         lat.step(args.warmup)
         lat.synchronize()
@@ -221,11 +225,12 @@ def run_ours(args, rank, world):
     value = nf * args.steps * world / (ms / 1e3) / 1e6
     peak, peak_kind = peaks()
     fused_ms = float(kms[2]) if kms[2] > 0 else float(kms.max())
-    achieved = ALGO_BYTES_FP32 * nf / (fused_ms / 1e3) / 1e9
-    step_bytes_rate = ALGO_BYTES_FP32 * nf / (ms / args.steps / 1e3) / 1e9
+    algo = ALGO_BYTES[args.storage]
+    achieved = algo * nf / (fused_ms / 1e3) / 1e9
+    step_bytes_rate = algo * nf / (ms / args.steps / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": measured_traffic("k_fused"), "kernel": "k_fused", "peak_kind": peak_kind,
-            "algorithmic_bytes_per_node": ALGO_BYTES_FP32, "kernel_ms": {names[k]: float(kms[k]) for k in range(5)},
+            "algorithmic_bytes_per_node": algo, "kernel_ms": {names[k]: float(kms[k]) for k in range(5)},
             "step_frac": step_bytes_rate / peak}
     del lat
     torch.cuda.synchronize()
@@ -234,7 +239,7 @@ def run_ours(args, rank, world):
     # upload), initial densities upload, K steps, fields and saturation read back
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lat2 = lbm.Lattice(solid, kernel=args.kernel, **kw)
+    lat2 = lbm.Lattice(solid, kernel=args.kernel, storage=args.storage, **kw)
     lat2.init_densities(r1, r2)
     lat2.step(args.steps)
     fields = lat2.fields(("rho1", "rho2"))
@@ -253,10 +258,11 @@ def run_ours(args, rank, world):
                "sample": "%d full steps of the %s workload (%.1f s)" % (done, WORKLOAD, cdt)}
     cfg = dict(cfg)
     cfg.update({"parallelism": "replicas" if world > 1 else "single", "kernel_schedule": args.kernel,
+                "storage": args.storage,
                 "voxel_mlups": nvox * args.steps * world / (ms / 1e3) / 1e6})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg, "roofline": roof,
+            "vs_baseline": None, "dtype": DTYPE[args.storage], "data": "synthetic", "config": cfg, "roofline": roof,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "saturation": {"S_w": sat[0], "S_nw_smooth": sat[1]}}
     if rank == 0:
@@ -273,6 +279,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--kernel", default="auto", choices=("auto", "split", "fused"))
+    ap.add_argument("--storage", default="fp32", choices=("fp32", "fp64", "fp16dev", "bf16dev"))
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

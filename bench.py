@@ -11,6 +11,13 @@ nodes; the all-voxel rate is in ``config``).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 run under torchrun: every rank runs an independent replica.
+
+``--workload batched_sweep_64`` instead times the batched sweep: 64
+independent sphere packs (edges 48..112, radius 4..8, porosity 0.35..0.45,
+viscosity ratio in {1, 5, 10, 50}, contact angle in {30, 60, 90, 120} deg)
+stepped together as one batch (three launches per step for all samples, CUDA
+graph replay, autotuned block size), next to the same samples stepped one
+after another as solo lattices; aggregate MLUPS over all fluid nodes.
 """
 import argparse
 import hashlib
@@ -53,6 +60,40 @@ def workload_setup():
            "M": 10, "theta_deg": 45, "G": G, "Pc": pc, "n_fluid": int((solid == 0).sum()),
            "lups_basis": "fluid nodes", "l2": "inputs larger than L2 (populations alone 146 MB)"}
     return solid, r1, r2, kw, cfg
+
+
+BATCH_WORKLOAD = "batched_sweep_64"
+
+
+def _pc_inlet(G=3.5, minor=0.03, pc=0.02):
+    p_out = (1.0 + minor) / 3.0 + G / 3.0 * minor
+    return (p_out + pc - minor / 3.0) / (1.0 / 3.0 + G / 3.0 * minor)
+
+
+def batch_setup(count=64):
+    """Geometries of the batched sweep, built in a spawn pool of host processes."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    from paper_2207_01534_gb300 import inputs
+
+    specs = inputs.batched_sweep(count)
+    workers = min(len(specs), os.cpu_count() or 1)
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        geo = list(ex.map(inputs.batched_sample, specs))
+    samples, states = [], []
+    for spec, (solid, r1, r2) in zip(specs, geo):
+        samples.append(dict(solid=solid, tau=inputs.tau_for_viscosity_ratio(spec["M"]), G=3.5,
+                            xi=inputs.xi_of_theta(spec["theta_deg"]), periodic=(1, 1, 0), open_axis=2,
+                            rho_in1=_pc_inlet(), rho_out2=1.0))
+        states.append((r1, r2))
+    nf = [int((kw["solid"] == 0).sum()) for kw in samples]
+    cfg = {"workload": BATCH_WORKLOAD, "samples": len(specs), "edges": [sp["n"] for sp in specs],
+           "n_fluid_total": int(sum(nf)), "n_voxels_total": int(sum(kw["solid"].size for kw in samples)),
+           "M": sorted({sp["M"] for sp in specs}), "theta_deg": sorted({sp["theta_deg"] for sp in specs}),
+           "Pc": 0.02, "reservoir": 6, "lups_basis": "fluid nodes",
+           "l2": "inputs larger than L2 (populations of all samples exceed 1 GB)"}
+    return samples, states, cfg
 
 
 class ClockSampler:
@@ -272,6 +313,97 @@ def run_ours(args, rank, world):
         dist.destroy_process_group()
 
 
+def run_batch(args, rank, world):
+    import tempfile
+
+    samples, states, cfg = batch_setup()
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2207_01534_gb300 import lbm
+
+    lbm.load()
+    nf = cfg["n_fluid_total"]
+    stream = torch.cuda.Stream()
+    cache = args.tune_cache or os.path.join(tempfile.gettempdir(), "lbm_autotune.json")
+    with torch.cuda.stream(stream):
+        b = lbm.Batch([dict(kw, storage=args.storage) for kw in samples], stream=stream.cuda_stream)
+        for smp, (r1, r2) in zip(b.samples, states):
+            smp.init_densities(r1, r2)
+        b.step(args.warmup)
+        block = b.autotune(cache)
+        b.step(2)
+        b.synchronize()
+        clocks = ClockSampler(local)
+        l0 = b.info()["launches"]
+        torch.cuda.synchronize()
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        b.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        launches = b.info()["launches"] - l0
+        ms = ev0.elapsed_time(ev1)
+        sats = [smp.saturation() for smp in b.samples]
+        assert np.isfinite(np.array(sats)).all()
+        b.close()
+        del b
+        torch.cuda.synchronize()
+
+        # the same samples as solo lattices stepped one after another
+        solo = []
+        for kw, (r1, r2) in zip(samples, states):
+            g = lbm.Lattice(kernel="split", storage=args.storage, stream=stream.cuda_stream, **kw)
+            g.init_densities(r1, r2)
+            g.step(args.warmup + 2)
+            solo.append(g)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for g in solo:
+            g.step(args.steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms_solo = ev0.elapsed_time(ev1)
+        for g in solo:
+            g.close()
+        del solo
+        torch.cuda.synchronize()
+
+    # end to end through the public API with host buffers
+    t0 = time.perf_counter()
+    b2 = lbm.Batch([dict(kw, storage=args.storage) for kw in samples])
+    for smp, (r1, r2) in zip(b2.samples, states):
+        smp.init_densities(r1, r2)
+    b2.step(args.steps)
+    s2 = [smp.saturation() for smp in b2.samples]
+    dt = time.perf_counter() - t0
+    b2.close()
+    h2d = sum(kw["solid"].nbytes + r1.nbytes + r2.nbytes for kw, (r1, r2) in zip(samples, states))
+    d2h = 32 * len(samples)
+    value = nf * args.steps / (ms / 1e3) / 1e6
+    peak, peak_kind = peaks()
+    algo = ALGO_BYTES[args.storage]
+    achieved = algo * nf / (ms / args.steps / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "kernel": "whole batched step (k_dens_batch + k_wall_batch + k_fused_batch)",
+            "peak_kind": peak_kind, "algorithmic_bytes_per_node": algo}
+    cfg = dict(cfg)
+    cfg.update({"parallelism": "single", "storage": args.storage, "block": block,
+                "solo_sequential_mlups": nf * args.steps / (ms_solo / 1e3) / 1e6,
+                "batch_over_solo": ms_solo / ms})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE[args.storage], "data": "synthetic", "config": cfg, "roofline": roof,
+            "cpu_baseline": None, "gpu_launches": int(launches), "clocks": clk,
+            "e2e": {"value": nf * args.steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+                    "d2h_bytes_per_step": d2h / args.steps}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,12 +414,16 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp64", "fp16dev", "bf16dev"))
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default=WORKLOAD, choices=(WORKLOAD, BATCH_WORKLOAD))
+    ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache (batched workload)")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps > 0
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == BATCH_WORKLOAD:
+        run_batch(args, rank, world)
     else:
         run_ours(args, rank, world)
 

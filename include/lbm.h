@@ -195,6 +195,47 @@ lbm_status lbm_synchronize(lbm_ctx *ctx);
 lbm_status lbm_get_info(const lbm_ctx *ctx, lbm_info *info);
 const char *lbm_last_error(const lbm_ctx *ctx);
 
+/* ---- Batches: many independent samples stepped together ------------------
+ * The drainage study of Section 4 runs one lattice per rock sample, contact
+ * angle and viscosity ratio; those lattices are independent, so a batch steps
+ * all of them with three launches per step (the density, wall and
+ * collide-and-stream passes of every sample), each block working on one
+ * sample.  Each sample's arithmetic is that of its solo run, node for node, so
+ * its results are bitwise those of the same lattice stepped alone.
+ *
+ * lbm_create_batch creates n sample lattices from geoms[k], params[k] (as
+ * lbm_create; kernel is forced to SPLIT, and every sample must use the same
+ * storage type) and the batch that owns them.  The samples are reached with
+ * lbm_batch_get and are initialised, read and retargeted (lbm_set_inlet) one
+ * by one; they are stepped only through the batch (lbm_step on a sample
+ * returns LBM_ERR_ARG), and all samples must be at the same step.  The batch
+ * itself accepts lbm_step, lbm_set_stream (the samples follow), lbm_synchronize
+ * (the first failing sample's status), lbm_get_info (sums over the samples),
+ * lbm_autotune and lbm_destroy (which destroys the samples; lbm_destroy on a
+ * sample does nothing).  On failure nothing is created and lbm_last_error(NULL)
+ * names the sample. */
+lbm_status lbm_create_batch(int32_t n, const lbm_geometry *geoms, const lbm_params *params, lbm_ctx **out);
+int32_t lbm_batch_size(const lbm_ctx *batch);
+lbm_status lbm_batch_get(lbm_ctx *batch, int32_t k, lbm_ctx **sample);
+
+/* lbm_step on a single lattice or a batch with the split schedule,
+ * reduce_every = 0 and n >= 4 replays two steps at a time from a CUDA graph,
+ * captured once on a private stream at the first even step after step 0 and
+ * recaptured after any change of the lattice's parameters.  Setting the
+ * environment variable LBM_NO_GRAPH disables it. */
+
+/* Autotuner: times a few steps of the context's own lattice (or batch) at
+ * each candidate block size of the split schedule (64, 128, 256 threads),
+ * keeps the fastest, and caches it in the JSON file cache_path (a flat object
+ * of "key": block pairs; the key names the GPU, compute capability, storage
+ * type, batch size and node counts).  A cached key is applied without timing.
+ * The state, step counter and status word are saved before the trial steps
+ * and put back afterwards (this needs a temporary copy of the populations).
+ * cache_path may be NULL (no cache); *block_out (may be NULL) receives the
+ * block size in use.  The single-pass schedule has a fixed block (its chunk)
+ * and is returned as is.  Synchronises. */
+lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t *block_out);
+
 /* Largest n accepted by lbm_saturation_static. */
 #define LBM_SATURATION_STATIC_MAX_N 16777216
 

@@ -42,7 +42,7 @@ struct lbm_ctx {
     void *(*alloc_fn)(size_t, void *) = nullptr;
     void (*free_fn)(void *, void *) = nullptr;
     void *alloc_user = nullptr;
-    std::vector<void *> allocs;
+    std::vector<std::pair<void *, size_t>> allocs;  // live device allocations and their sizes
     int64_t step = 0, launches = 0, bytes = 0;
     lbm_status sticky = LBM_OK;
     std::string err;
@@ -56,6 +56,20 @@ struct lbm_ctx {
     bool have_ev = false;
     // single-pass schedule
     PipeState ps{};
+    int block = 256;                  // threads per block of the split-schedule passes (autotuned)
+    // batch contexts: samples stepped together by batched launches
+    std::vector<lbm_ctx *> subs;
+    lbm_ctx *parent = nullptr;
+    DevState *d_states = nullptr;
+    int2 *d_map_n = nullptr, *d_map_w = nullptr;
+    int n_map_n = 0, n_map_w = 0, map_block = 0;
+    bool states_dirty = true;
+    // CUDA graph of two split-schedule steps, captured on a private stream
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool graph_dirty = true;
+    int64_t graph_launches = 0;  // kernels per replay
+    size_t f_bytes = 0, rest_bytes = 0, bc_bytes = 0;  // the state a step reads and writes
     std::vector<uint8_t> solid_host;  // the mask, for host-side statistics
     void *psi_alt = nullptr;
     int pipe_grid = 0;
@@ -123,7 +137,7 @@ void *dalloc(lbm_ctx *c, size_t bytes)
         ptr = nullptr;
     }
     if (ptr) {
-        c->allocs.push_back(ptr);
+        c->allocs.push_back({ptr, bytes});
         c->bytes += (int64_t)bytes;
     }
     return ptr;
@@ -133,7 +147,8 @@ void dfree(lbm_ctx *c, void *ptr)
 {
     if (!ptr) return;
     for (size_t k = 0; k < c->allocs.size(); ++k)
-        if (c->allocs[k] == ptr) {
+        if (c->allocs[k].first == ptr) {
+            c->bytes -= (int64_t)c->allocs[k].second;
             c->allocs.erase(c->allocs.begin() + (long)k);
             break;
         }
@@ -199,11 +214,33 @@ lbm_status check_launch(lbm_ctx *c, const char *where)
 lbm_status device_status(lbm_ctx *c)
 {
     if (c->sticky != LBM_OK) return c->sticky;
+    for (lbm_ctx *q : c->subs) {
+        lbm_status st = device_status(q);
+        if (st != LBM_OK) return fail(c, st, "a sample of the batch: " + q->err);
+    }
     const int f = c->h_flag ? *(volatile int *)c->h_flag : 0;
     if (f & 1) return fail(c, LBM_ERR_NONFINITE, "non-finite density found by the periodic check");
     if (f & 2) return fail(c, LBM_ERR_DRIFT, "mass drift above drift_limit");
     if (f & 4) return fail(c, LBM_ERR_TIMEOUT, "a bounded device wait gave up");
     return LBM_OK;
+}
+
+// Host-side change of a lattice's parameters: a captured graph holds the old
+// kernel arguments, and a batch holds a device copy of every sample's state.
+void touch(lbm_ctx *c)
+{
+    c->graph_dirty = true;
+    if (c->parent) {
+        c->parent->states_dirty = true;
+        c->parent->graph_dirty = true;
+    }
+}
+
+// A batch has no lattice of its own: its samples are read and written through
+// lbm_batch_get.
+lbm_status no_batch(lbm_ctx *c, const char *what)
+{
+    return fail(c, LBM_ERR_ARG, std::string(what) + " takes a lattice; use lbm_batch_get for a sample of a batch");
 }
 
 void run_reduce(lbm_ctx *c)
@@ -255,11 +292,11 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
     dispatch(c, [&](auto tag) {
         using TS = decltype(tag);
         if (ev) cudaEventRecord(ev[0], st);
-        Ops<TS>::dens(c->s, par, c->step > 0, st);
+        Ops<TS>::dens(c->s, par, c->step > 0, st, c->block);
         if (ev) cudaEventRecord(ev[1], st);
-        Ops<TS>::wall(c->s, st);
+        Ops<TS>::wall(c->s, st, c->block);
         if (ev) cudaEventRecord(ev[2], st);
-        Ops<TS>::fused(c->s, par, st);
+        Ops<TS>::fused(c->s, par, st, c->block);
         if (ev) cudaEventRecord(ev[3], st);
         if (ev) cudaEventRecord(ev[4], st);
     });
@@ -272,6 +309,306 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
                                  c->d_flag);
         c->launches += 1;
     }
+}
+
+// Sample states and block maps of a batch.  map entry b = (sample, block
+// within the sample) for the node passes and for the wall pass.
+lbm_status build_maps(lbm_ctx *c, int block)
+{
+    std::vector<int2> mn, mw;
+    for (size_t k = 0; k < c->subs.size(); ++k) {
+        const DevState &s = c->subs[k]->s;
+        for (int j = 0; j < (s.n_fluid + block - 1) / block; ++j) mn.push_back(make_int2((int)k, j));
+        for (int j = 0; j < (s.n_wall + block - 1) / block; ++j) mw.push_back(make_int2((int)k, j));
+    }
+    if (c->d_map_n) dfree(c, c->d_map_n);
+    if (c->d_map_w) dfree(c, c->d_map_w);
+    c->d_map_n = (int2 *)dalloc(c, std::max<size_t>(1, mn.size()) * sizeof(int2));
+    c->d_map_w = (int2 *)dalloc(c, std::max<size_t>(1, mw.size()) * sizeof(int2));
+    if (!c->d_map_n || !c->d_map_w) return fail(c, LBM_ERR_ALLOC, "batch block maps");
+    cudaError_t e = cudaSuccess;
+    if (!mn.empty()) e = cudaMemcpy(c->d_map_n, mn.data(), mn.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !mw.empty())
+        e = cudaMemcpy(c->d_map_w, mw.data(), mw.size() * sizeof(int2), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batch block maps");
+    c->n_map_n = (int)mn.size();
+    c->n_map_w = (int)mw.size();
+    c->map_block = block;
+    c->graph_dirty = true;
+    return LBM_OK;
+}
+
+lbm_status upload_states(lbm_ctx *c)
+{
+    std::vector<DevState> h(c->subs.size());
+    for (size_t k = 0; k < c->subs.size(); ++k) h[k] = c->subs[k]->s;
+    cudaError_t e = cudaMemcpyAsync(c->d_states, h.data(), h.size() * sizeof(DevState), cudaMemcpyHostToDevice,
+                                    c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);  // h is released below
+    if (e != cudaSuccess) return cuda_fail(c, e, "batch states");
+    c->states_dirty = false;
+    return LBM_OK;
+}
+
+// One step of a batch: the three split-schedule passes of every sample in
+// three launches.
+void enqueue_batch_step(lbm_ctx *c)
+{
+    lbm_ctx *s0 = c->subs[0];
+    const int par = (int)(s0->step & 1);
+    cudaStream_t st = c->stream;
+    dispatch(c, [&](auto tag) {
+        using TS = decltype(tag);
+        Ops<TS>::dens_batch(c->d_states, c->d_map_n, c->n_map_n, par, s0->step > 0, st, c->map_block);
+        Ops<TS>::wall_batch(c->d_states, c->d_map_w, c->n_map_w, st, c->map_block);
+        Ops<TS>::fused_batch(c->d_states, c->d_map_n, c->n_map_n, par, st, c->map_block);
+    });
+    c->launches += 3;
+    for (lbm_ctx *q : c->subs) {
+        q->step++;
+        if (q->p.reduce_every > 0 && q->step % q->p.reduce_every == 0) {
+            run_reduce(q);
+            k_check<<<1, 1, 0, st>>>(q->d_red, q->mass0[0], q->mass0[1], q->p.drift_limit, q->s.open_z ? 0 : 1,
+                                     q->d_flag);
+            c->launches += q->launches;  // counted on the batch
+            q->launches = 0;
+            c->launches += 1;
+        }
+    }
+    c->step++;
+}
+
+bool any_reduce(const lbm_ctx *c)
+{
+    if (c->p.reduce_every > 0) return true;
+    for (const lbm_ctx *q : c->subs)
+        if (q->p.reduce_every > 0) return true;
+    return false;
+}
+
+int64_t cur_step(const lbm_ctx *c) { return c->subs.empty() ? c->step : c->subs[0]->step; }
+
+void step_once(lbm_ctx *c)
+{
+    if (c->subs.empty())
+        enqueue_step(c, nullptr);
+    else
+        enqueue_batch_step(c);
+}
+
+// Capture two steps (even parity, after the first step) into a CUDA graph on a
+// private stream; the graph is then launched on the context's stream.
+lbm_status ensure_graph(lbm_ctx *c)
+{
+    if (c->graph && !c->graph_dirty) return LBM_OK;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "graph stream");
+    const cudaStream_t user = c->stream;
+    const int64_t step0 = c->step, launches0 = c->launches;
+    std::vector<int64_t> sub_steps;
+    for (lbm_ctx *q : c->subs) sub_steps.push_back(q->step);
+    c->stream = c->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        step_once(c);
+        step_once(c);
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &g) : e;
+    c->stream = user;
+    c->step = step0;
+    for (size_t k = 0; k < c->subs.size(); ++k) c->subs[k]->step = sub_steps[k];
+    c->graph_launches = c->launches - launches0;
+    c->launches = launches0;
+    if (e2 == cudaSuccess) e2 = cudaGraphInstantiate(&c->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        c->graph = nullptr;
+        return cuda_fail(c, e2, "graph capture");
+    }
+    c->graph_dirty = false;
+    return LBM_OK;
+}
+
+void destroy_ctx(lbm_ctx *c)
+{
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    for (lbm_ctx *q : c->subs) destroy_ctx(q);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    std::vector<std::pair<void *, size_t>> a = c->allocs;
+    for (auto &q : a) dfree(c, q.first);
+    if (c->h_flag) cudaFreeHost(c->h_flag);
+    if (c->have_ev)
+        for (auto &ev : c->ev) cudaEventDestroy(ev);
+    delete c;
+}
+
+// ---- autotuner ------------------------------------------------------------
+// Sweeps the threads per block of the split schedule's three passes over a
+// few timed steps of the context's own lattice(s), keeps the fastest and
+// caches it in a JSON object {"key": block, ...} keyed by GPU, storage type,
+// batch size and node counts.
+constexpr int kTuneBlocks[] = {64, 128, 256};
+constexpr int kTuneWarm = 2, kTuneSteps = 8;
+
+std::string tune_key(const lbm_ctx *c)
+{
+    cudaDeviceProp prop{};
+    cudaGetDeviceProperties(&prop, c->device);
+    std::string name = prop.name;
+    for (char &ch : name)
+        if (ch == '"' || ch == '\\' || ch < 32) ch = '_';
+    static const char *kStore[] = {"fp32", "fp64", "fp16dev", "bf16dev"};
+    int64_t nf = c->s.n_fluid, nw = c->s.n_wall;
+    for (const lbm_ctx *q : c->subs) {
+        nf += q->s.n_fluid;
+        nw += q->s.n_wall;
+    }
+    char buf[256];
+    std::snprintf(buf, sizeof(buf), "|sm_%d%d|%s|samples=%d|fluid=%lld|walls=%lld", prop.major, prop.minor,
+                  kStore[c->storage & 3], c->subs.empty() ? 1 : (int)c->subs.size(), (long long)nf, (long long)nw);
+    return name + buf;
+}
+
+// Minimal reader of the cache: "string": integer pairs of one flat object.
+std::vector<std::pair<std::string, int>> read_cache(const char *path)
+{
+    std::vector<std::pair<std::string, int>> kv;
+    FILE *fp = path ? std::fopen(path, "rb") : nullptr;
+    if (!fp) return kv;
+    std::string txt;
+    char buf[4096];
+    size_t n;
+    while ((n = std::fread(buf, 1, sizeof(buf), fp)) > 0) txt.append(buf, n);
+    std::fclose(fp);
+    size_t i = 0;
+    while (true) {
+        size_t a = txt.find('"', i);
+        if (a == std::string::npos) break;
+        size_t b = txt.find('"', a + 1);
+        if (b == std::string::npos) break;
+        size_t colon = txt.find(':', b);
+        if (colon == std::string::npos) break;
+        char *end = nullptr;
+        long v = std::strtol(txt.c_str() + colon + 1, &end, 10);
+        if (end == txt.c_str() + colon + 1) break;
+        kv.push_back({txt.substr(a + 1, b - a - 1), (int)v});
+        i = (size_t)(end - txt.c_str());
+    }
+    return kv;
+}
+
+bool write_cache(const char *path, const std::vector<std::pair<std::string, int>> &kv)
+{
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *fp = std::fopen(tmp.c_str(), "wb");
+    if (!fp) return false;
+    std::fputs("{\n", fp);
+    for (size_t k = 0; k < kv.size(); ++k)
+        std::fprintf(fp, "  \"%s\": %d%s\n", kv[k].first.c_str(), kv[k].second, k + 1 < kv.size() ? "," : "");
+    std::fputs("}\n", fp);
+    const bool ok = std::fclose(fp) == 0;
+    return ok && std::rename(tmp.c_str(), path) == 0;
+}
+
+lbm_status apply_block(lbm_ctx *c, int block)
+{
+    if (!c->subs.empty()) return build_maps(c, block);
+    c->block = block;
+    c->graph_dirty = true;
+    return LBM_OK;
+}
+
+// Time kTuneSteps steps at each candidate, from a saved copy of the state
+// that is put back afterwards (with the step counters and status words).
+lbm_status tune(lbm_ctx *c, int *best)
+{
+    std::vector<lbm_ctx *> lat = c->subs.empty() ? std::vector<lbm_ctx *>{c} : c->subs;
+    struct Saved {
+        void *buf;
+        int64_t step;
+        int flag;
+    };
+    std::vector<Saved> saved;
+    lbm_status st = LBM_OK;
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_autotune");
+    for (lbm_ctx *q : lat) {
+        const size_t tot = q->f_bytes + q->rest_bytes + q->bc_bytes;
+        char *b = (char *)dalloc(q, tot);
+        if (!b) {
+            st = fail(c, LBM_ERR_ALLOC, "lbm_autotune: state copy");
+            break;
+        }
+        saved.push_back({b, q->step, q->h_flag ? *q->h_flag : 0});
+        e = cudaMemcpyAsync(b, q->s.f, q->f_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b + q->f_bytes, q->s.rest, q->rest_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess && q->bc_bytes)
+            e = cudaMemcpyAsync(b + q->f_bytes + q->rest_bytes, q->s.bc, q->bc_bytes, cudaMemcpyDeviceToDevice,
+                                c->stream);
+        if (e != cudaSuccess) {
+            st = cuda_fail(c, e, "lbm_autotune: state copy");
+            break;
+        }
+    }
+    const int64_t step0 = c->step;
+    const int block0 = c->subs.empty() ? c->block : c->map_block;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    float best_ms = 0.f;
+    *best = block0;
+    if (st == LBM_OK && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess))
+        st = cuda_fail(c, cudaGetLastError(), "lbm_autotune: events");
+    for (int cand : kTuneBlocks) {
+        if (st != LBM_OK) break;
+        st = apply_block(c, cand);
+        if (st != LBM_OK) break;
+        for (int k = 0; k < kTuneWarm; ++k) step_once(c);
+        cudaEventRecord(ev[0], c->stream);
+        for (int k = 0; k < kTuneSteps; ++k) step_once(c);
+        cudaEventRecord(ev[1], c->stream);
+        e = cudaEventSynchronize(ev[1]);
+        if (e != cudaSuccess) {
+            st = cuda_fail(c, e, "lbm_autotune: timed steps");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        if (best_ms == 0.f || ms < best_ms) {
+            best_ms = ms;
+            *best = cand;
+        }
+    }
+    for (cudaEvent_t x : ev)
+        if (x) cudaEventDestroy(x);
+    // put the state back
+    for (size_t k = 0; k < saved.size(); ++k) {
+        lbm_ctx *q = lat[k];
+        char *b = (char *)saved[k].buf;
+        cudaMemcpyAsync(q->s.f, b, q->f_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        cudaMemcpyAsync(q->s.rest, b + q->f_bytes, q->rest_bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (q->bc_bytes)
+            cudaMemcpyAsync(q->s.bc, b + q->f_bytes + q->rest_bytes, q->bc_bytes, cudaMemcpyDeviceToDevice,
+                            c->stream);
+    }
+    e = cudaStreamSynchronize(c->stream);
+    for (size_t k = 0; k < saved.size(); ++k) {
+        lbm_ctx *q = lat[k];
+        dfree(q, saved[k].buf);
+        q->step = saved[k].step;
+        if (q->h_flag) *q->h_flag = saved[k].flag;
+    }
+    c->step = step0;
+    if (st == LBM_OK && e != cudaSuccess) st = cuda_fail(c, e, "lbm_autotune: restore");
+    if (st != LBM_OK) apply_block(c, block0);
+    return st;
 }
 
 }  // namespace
@@ -466,6 +803,9 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     void *d_wmask = A((size_t)NW * 4);
     void *d_winv = A((size_t)NW * szc);
     void *d_wxi = A((size_t)NW * szc);
+    c->f_bytes = (size_t)18 * npad * 2 * sz;
+    c->rest_bytes = (size_t)npad * 2 * szc;
+    c->bc_bytes = open_z ? (size_t)2 * 2 * 5 * nxy * sz : 0;
     if (open_z) {
         s.bc = A((size_t)2 * 2 * 5 * nxy * sz);
         c->d_frozen = (double *)A((size_t)2 * 5 * nxy * 8);
@@ -627,21 +967,16 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
 
 void lbm_destroy(lbm_ctx *c)
 {
-    if (!c) return;
-    if (c->stream) cudaStreamSynchronize(c->stream);
-    else cudaDeviceSynchronize();
-    std::vector<void *> a = c->allocs;
-    for (void *q : a) dfree(c, q);
-    if (c->h_flag) cudaFreeHost(c->h_flag);
-    if (c->have_ev)
-        for (auto &ev : c->ev) cudaEventDestroy(ev);
-    delete c;
+    if (!c || c->parent) return;  // sample contexts belong to their batch
+    destroy_ctx(c);
 }
 
 lbm_status lbm_init_densities(lbm_ctx *c, const double *rho1, const double *rho2)
 {
     if (!c || !rho1 || !rho2) return LBM_ERR_ARG;
+    if (!c->subs.empty()) return no_batch(c, "lbm_init_densities");
     choose_rho_ref(c, rho1, rho2, 0);
+    touch(c);
     const size_t bytes = (size_t)c->nv * 8;
     double *d = (double *)dalloc(c, 2 * bytes);
     if (!d) return fail(c, LBM_ERR_ALLOC, "temporary density buffer");
@@ -669,7 +1004,9 @@ lbm_status lbm_init_densities(lbm_ctx *c, const double *rho1, const double *rho2
 lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
 {
     if (!c || !f) return LBM_ERR_ARG;
+    if (!c->subs.empty()) return no_batch(c, "lbm_set_populations");
     choose_rho_ref(c, f, f + 19 * c->nv, c->nv);
+    touch(c);
     const size_t bytes = (size_t)38 * c->nv * 8;
     double *d = (double *)dalloc(c, bytes);
     if (!d) return fail(c, LBM_ERR_ALLOC, "temporary population buffer");
@@ -696,6 +1033,7 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
 lbm_status lbm_get_populations(lbm_ctx *c, double *f)
 {
     if (!c || !f) return LBM_ERR_ARG;
+    if (!c->subs.empty()) return no_batch(c, "lbm_get_populations");
     const size_t bytes = (size_t)38 * c->nv * 8;
     double *d = (double *)dalloc(c, bytes);
     if (!d) return fail(c, LBM_ERR_ALLOC, "temporary population buffer");
@@ -721,14 +1059,98 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f)
 lbm_status lbm_step(lbm_ctx *c, int64_t n)
 {
     if (!c || n < 0) return LBM_ERR_ARG;
-    for (int64_t k = 0; k < n; ++k) enqueue_step(c, nullptr);
+    if (c->parent) return fail(c, LBM_ERR_ARG, "a sample of a batch is stepped through its batch");
+    if (!c->subs.empty()) {
+        for (lbm_ctx *q : c->subs)
+            if (q->step != c->subs[0]->step) return fail(c, LBM_ERR_ARG, "the samples of a batch are at different steps");
+        if (c->states_dirty) {
+            lbm_status st = upload_states(c);
+            if (st != LBM_OK) return st;
+        }
+    }
+    int64_t k = 0;
+    const bool graphs = c->kernel == LBM_KERNEL_SPLIT && !any_reduce(c) && n >= 4 &&
+                        std::getenv("LBM_NO_GRAPH") == nullptr;
+    if (graphs) {
+        // the first step (no plane extrapolation yet) and odd parities run plain
+        while (k < n && (cur_step(c) == 0 || (cur_step(c) & 1))) {
+            step_once(c);
+            ++k;
+        }
+        if (n - k >= 2 && ensure_graph(c) == LBM_OK) {
+            for (; n - k >= 2; k += 2) {
+                cudaGraphLaunch(c->graph, c->stream);
+                c->step += 2;
+                for (lbm_ctx *q : c->subs) q->step += 2;
+                c->launches += c->graph_launches;
+            }
+        }
+    }
+    for (; k < n; ++k) step_once(c);
     lbm_status st = check_launch(c, "lbm_step");
     return st != LBM_OK ? st : device_status(c);
+}
+
+lbm_status lbm_create_batch(int32_t n, const lbm_geometry *geoms, const lbm_params *params, lbm_ctx **out)
+{
+    if (!out) return fail(nullptr, LBM_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n <= 0 || !geoms || !params) return fail(nullptr, LBM_ERR_ARG, "need n > 0 geometries and parameter sets");
+    std::vector<lbm_ctx *> subs;
+    for (int32_t k = 0; k < n; ++k) {
+        lbm_params pk = params[k];
+        if (pk.kernel == LBM_KERNEL_FUSED) pk.kernel = LBM_KERNEL_SPLIT;
+        lbm_ctx *q = nullptr;
+        lbm_status st = lbm_create(&geoms[k], &pk, &q);
+        if (st == LBM_OK && q->storage != (subs.empty() ? q->storage : subs[0]->storage)) {
+            lbm_destroy(q);
+            st = fail(nullptr, LBM_ERR_ARG, "all samples of a batch need the same storage type");
+        }
+        if (st != LBM_OK) {
+            g_create_err = "sample " + std::to_string(k) + ": " + g_create_err;
+            for (lbm_ctx *r : subs) destroy_ctx(r);
+            return st;
+        }
+        subs.push_back(q);
+    }
+    lbm_ctx *c = new lbm_ctx();
+    cudaGetDevice(&c->device);
+    c->alloc_fn = g_alloc;
+    c->free_fn = g_free;
+    c->alloc_user = g_alloc_user;
+    c->storage = subs[0]->storage;
+    c->kernel = LBM_KERNEL_SPLIT;
+    lbm_default_params(&c->p);
+    c->subs = subs;
+    for (lbm_ctx *q : subs) q->parent = c;
+    c->d_states = (DevState *)dalloc(c, (size_t)n * sizeof(DevState));
+    if (!c->d_states) {
+        destroy_ctx(c);
+        return fail(nullptr, LBM_ERR_ALLOC, "batch states");
+    }
+    if (build_maps(c, 256) != LBM_OK) {
+        g_create_err = c->err;
+        destroy_ctx(c);
+        return LBM_ERR_ALLOC;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+int32_t lbm_batch_size(const lbm_ctx *c) { return c ? (int32_t)c->subs.size() : 0; }
+
+lbm_status lbm_batch_get(lbm_ctx *c, int32_t k, lbm_ctx **sample)
+{
+    if (!c || !sample || k < 0 || k >= (int32_t)c->subs.size()) return LBM_ERR_ARG;
+    *sample = c->subs[(size_t)k];
+    return LBM_OK;
 }
 
 lbm_status lbm_step_timed(lbm_ctx *c, int64_t n, double *kernel_ms, int32_t nk)
 {
     if (!c || n < 0 || (nk > 0 && !kernel_ms)) return LBM_ERR_ARG;
+    if (!c->subs.empty()) return no_batch(c, "lbm_step_timed");
+    if (c->parent) return fail(c, LBM_ERR_ARG, "a sample of a batch is stepped through its batch");
     if (!c->have_ev) {
         for (auto &ev : c->ev) cudaEventCreate(&ev);
         c->have_ev = true;
@@ -757,6 +1179,7 @@ lbm_status lbm_step_timed(lbm_ctx *c, int64_t n, double *kernel_ms, int32_t nk)
 lbm_status lbm_read_fields(lbm_ctx *c, uint32_t mask, double *out, size_t n_per_field)
 {
     if (!c || !out) return LBM_ERR_ARG;
+    if (!c->subs.empty()) return no_batch(c, "lbm_read_fields");
     if (n_per_field < (size_t)c->nv) return fail(c, LBM_ERR_ARG, "n_per_field is smaller than nx*ny*nz");
     const size_t bytes = (size_t)6 * c->nv * 8;
     double *d = (double *)dalloc(c, bytes);
@@ -789,6 +1212,7 @@ lbm_status lbm_read_fields(lbm_ctx *c, uint32_t mask, double *out, size_t n_per_
 lbm_status lbm_saturation(lbm_ctx *c, double out[4])
 {
     if (!c || !out) return LBM_ERR_ARG;
+    if (!c->subs.empty()) return no_batch(c, "lbm_saturation");
     run_reduce(c);
     lbm_status st = check_launch(c, "lbm_saturation");
     double red[kReduceSlots];
@@ -805,8 +1229,10 @@ lbm_status lbm_saturation(lbm_ctx *c, double out[4])
 lbm_status lbm_set_inlet(lbm_ctx *c, double rho_in1)
 {
     if (!c) return LBM_ERR_ARG;
+    if (!c->subs.empty()) return no_batch(c, "lbm_set_inlet");
     c->p.rho_in1 = rho_in1;
     c->s.rho_in1 = rho_in1;
+    touch(c);
     return LBM_OK;
 }
 
@@ -814,6 +1240,7 @@ lbm_status lbm_set_stream(lbm_ctx *c, void *stream)
 {
     if (!c) return LBM_ERR_ARG;
     c->stream = (cudaStream_t)stream;
+    for (lbm_ctx *q : c->subs) q->stream = (cudaStream_t)stream;
     return LBM_OK;
 }
 
@@ -837,9 +1264,54 @@ lbm_status lbm_get_info(const lbm_ctx *c, lbm_info *info)
     info->n_voxels = c->nv;
     info->step = c->step;
     info->device_bytes = c->bytes;
+    for (const lbm_ctx *q : c->subs) {  // a batch reports the sum over its samples
+        info->n_fluid += q->s.n_fluid;
+        info->n_wall += q->s.n_wall;
+        info->n_voxels += q->nv;
+        info->device_bytes += q->bytes;
+        info->step = q->step;
+    }
     info->launches = c->launches;
     info->storage = c->storage;
     info->kernel = c->kernel;
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_ctx *c, const char *cache_path, int32_t *block_out)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (c->parent) return fail(c, LBM_ERR_ARG, "a sample of a batch is tuned through its batch");
+    if (c->kernel == LBM_KERNEL_FUSED) {  // the single-pass schedule's block is its chunk
+        if (block_out) *block_out = kChunk;
+        return LBM_OK;
+    }
+    const std::string key = tune_key(c);
+    std::vector<std::pair<std::string, int>> kv = read_cache(cache_path);
+    for (auto &e : kv)
+        if (e.first == key) {
+            for (int cand : kTuneBlocks)
+                if (cand == e.second) {
+                    lbm_status st = apply_block(c, cand);
+                    if (st == LBM_OK && block_out) *block_out = cand;
+                    return st;
+                }
+        }
+    int best = 0;
+    lbm_status st = tune(c, &best);
+    if (st != LBM_OK) return st;
+    st = apply_block(c, best);
+    if (st != LBM_OK) return st;
+    if (block_out) *block_out = best;
+    if (cache_path && *cache_path) {
+        bool found = false;
+        for (auto &e : kv)
+            if (e.first == key) {
+                e.second = best;
+                found = true;
+            }
+        if (!found) kv.push_back({key, best});
+        if (!write_cache(cache_path, kv)) return fail(c, LBM_ERR_ARG, "lbm_autotune: cannot write the cache file");
+    }
     return LBM_OK;
 }
 

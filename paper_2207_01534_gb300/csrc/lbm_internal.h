@@ -91,9 +91,16 @@ struct PipeState {
 template <typename TS>
 struct Ops {
     // densities into psi; neem != 0 first applies the open-plane extrapolation
-    static void dens(const DevState &s, int parity, int neem, cudaStream_t st);
-    static void wall(const DevState &s, cudaStream_t st);
-    static void fused(const DevState &s, int parity, cudaStream_t st);
+    static void dens(const DevState &s, int parity, int neem, cudaStream_t st, int block = 256);
+    static void wall(const DevState &s, cudaStream_t st, int block = 256);
+    static void fused(const DevState &s, int parity, cudaStream_t st, int block = 256);
+    // the same three passes over many samples in one launch each: states[k] is
+    // sample k; map[b] = (sample, block within the sample) for launch block b
+    static void dens_batch(const DevState *states, const int2 *map, int nblocks, int parity, int neem,
+                           cudaStream_t st, int block);
+    static void wall_batch(const DevState *states, const int2 *map, int nblocks, cudaStream_t st, int block);
+    static void fused_batch(const DevState *states, const int2 *map, int nblocks, int parity, cudaStream_t st,
+                            int block);
     static void plane(const DevState &s, int parity_next, cudaStream_t st);
     // rest equilibrium from device densities rho[2][nv] (double); parity-0 layout
     static void init_eq(const DevState &s, const double *rho, cudaStream_t st);

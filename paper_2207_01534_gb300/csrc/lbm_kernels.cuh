@@ -177,30 +177,30 @@ struct Traits16 {
     __device__ static __forceinline__ S2 quant(C2 v, C2 ref)
     {
         S2 h;
-        from_float2(make_float2(v.x - ref.x, v.y - ref.y), &h);
+        from_float2(make_float2(__fsub_rn(v.x, ref.x), __fsub_rn(v.y, ref.y)), &h);
         return h;
     }
     __device__ static __forceinline__ C2 dequant(S2 q, C2 ref)
     {
         const float2 d = to_float2(q);
-        return make_float2(ref.x + d.x, ref.y + d.y);
+        return make_float2(__fadd_rn(ref.x, d.x), __fadd_rn(ref.y, d.y));
     }
     __device__ static __forceinline__ C2 load(const S2 *p, C2 ref)
     {
         const float2 d = unpack(__ldg(reinterpret_cast<const unsigned *>(p)));
-        return make_float2(ref.x + d.x, ref.y + d.y);
+        return make_float2(__fadd_rn(ref.x, d.x), __fadd_rn(ref.y, d.y));
     }
     __device__ static __forceinline__ C2 load_cg(const S2 *p, C2 ref)
     {
         const float2 d = unpack(__ldcg(reinterpret_cast<const unsigned *>(p)));
-        return make_float2(ref.x + d.x, ref.y + d.y);
+        return make_float2(__fadd_rn(ref.x, d.x), __fadd_rn(ref.y, d.y));
     }
     __device__ static __forceinline__ void store(S2 *p, C2 v, C2 ref) { *p = quant(v, ref); }
     __device__ static __forceinline__ void store_q(S2 *p, S2 q) { *p = q; }
     __device__ static __forceinline__ void store1(S2 *p, int sg, C v, C ref)
     {
         H1 *h = reinterpret_cast<H1 *>(p) + sg;
-        from_float(v - ref, h);
+        from_float(__fsub_rn(v, ref), h);
     }
     // the stored deviation itself, as FP32
     template <bool L2ONLY>
@@ -220,8 +220,13 @@ template <typename TS>
 __device__ __forceinline__ typename Traits<TS>::C2 ref_of(const DevState &s, int i)
 {
     using C = typename Traits<TS>::C;
-    if (!Traits<TS>::kDev) return mk2(C(0), C(0));
-    return mk2(wgt<C>(i) * (C)s.rref1, wgt<C>(i) * (C)s.rref2);
+    if constexpr (!Traits<TS>::kDev) {
+        return mk2(C(0), C(0));
+    } else {
+        // explicitly rounded (never contracted into a later add), so every
+        // kernel that dequantises gets the same bits
+        return mk2(__fmul_rn(wgt<C>(i), (C)s.rref1), __fmul_rn(wgt<C>(i), (C)s.rref2));
+    }
 }
 
 // Rest-population pair of node n, kept at compute precision.  With deviation
@@ -524,10 +529,9 @@ __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb
 // neem = 0 skips the extrapolation (the state is an initial state that the
 // first step must see unchanged).
 template <typename TS, int P>
-__global__ void __launch_bounds__(256) k_dens(DevState s, int neem)
+__device__ __forceinline__ void dens_pass_node(int t, const DevState &s, int neem)
 {
     using C2 = typename Traits<TS>::C2;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= s.n_fluid) return;
     const int n = s.n_fluid - 1 - t;
     const uint32_t pv = s.pvox[n];
@@ -541,6 +545,12 @@ __global__ void __launch_bounds__(256) k_dens(DevState s, int neem)
     C2 f[19], dm;
     load_pops<TS, P>(f, dm, n, pv, fl, b, s);
     reinterpret_cast<C2 *>(s.psi)[pv] = density_of<TS>(dm, s);
+}
+
+template <typename TS, int P>
+__global__ void __launch_bounds__(256) k_dens(DevState s, int neem)
+{
+    dens_pass_node<TS, P>(blockIdx.x * blockDim.x + threadIdx.x, s, neem);
 }
 
 // Eq. 15 at one wall voxel: rho-tilde^sigma = chi^sigma * (sum of w_i rho^sigma
@@ -673,6 +683,51 @@ __global__ void __launch_bounds__(128) k_plane(DevState s)
     const int nb = s.cidx[pvb];
     if (nb < 0) return;
     neem_node<TS, PN, false>(plane, p, nb, pvb, s.nflags[nb], s);
+}
+
+// ---------------------------------------------------------------------------
+// Batched kernels: one launch covers the blocks of many samples.  map[b] =
+// (sample k, block index within the sample); the block copies states[k] to
+// shared memory and works on that sample exactly like the single-sample
+// kernel (same per-node functions, same results).
+
+__device__ __forceinline__ const DevState &stage_state(const DevState *states, int k, DevState *sh)
+{
+    const int words = (int)(sizeof(DevState) / 4);
+    const unsigned *src = reinterpret_cast<const unsigned *>(states + k);
+    unsigned *dst = reinterpret_cast<unsigned *>(sh);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) dst[w] = __ldg(src + w);
+    __syncthreads();
+    return *sh;
+}
+
+template <typename TS, int P>
+__global__ void __launch_bounds__(256) k_dens_batch(const DevState *states, const int2 *map, int neem)
+{
+    __shared__ __align__(16) DevState sh;
+    const int2 m = map[blockIdx.x];
+    const DevState &s = stage_state(states, m.x, &sh);
+    dens_pass_node<TS, P>(m.y * blockDim.x + threadIdx.x, s, neem && s.open_z);
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(256) k_wall_batch(const DevState *states, const int2 *map)
+{
+    __shared__ __align__(16) DevState sh;
+    const int2 m = map[blockIdx.x];
+    const DevState &s = stage_state(states, m.x, &sh);
+    const int w = m.y * blockDim.x + threadIdx.x;
+    if (w < s.n_wall) wall_node<TS, false>(w, s, s.psi);
+}
+
+template <typename TS, int P>
+__global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused_batch(const DevState *states, const int2 *map)
+{
+    __shared__ __align__(16) DevState sh;
+    const int2 m = map[blockIdx.x];
+    const DevState &s = stage_state(states, m.x, &sh);
+    const int n = m.y * blockDim.x + threadIdx.x;
+    if (n < s.n_fluid) fused_node<TS, P>(n, s);
 }
 
 // ---------------------------------------------------------------------------

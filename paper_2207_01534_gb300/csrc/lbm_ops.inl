@@ -7,26 +7,50 @@ namespace lbm {
 static inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 template <typename TS>
-void Ops<TS>::dens(const DevState &s, int parity, int neem, cudaStream_t st)
+void Ops<TS>::dens(const DevState &s, int parity, int neem, cudaStream_t st, int block)
 {
     if (s.n_fluid == 0) return;
-    if (parity) k_dens<TS, 1><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, neem && s.open_z);
-    else k_dens<TS, 0><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, neem && s.open_z);
+    if (parity) k_dens<TS, 1><<<grid_for(s.n_fluid, block), block, 0, st>>>(s, neem && s.open_z);
+    else k_dens<TS, 0><<<grid_for(s.n_fluid, block), block, 0, st>>>(s, neem && s.open_z);
 }
 
 template <typename TS>
-void Ops<TS>::wall(const DevState &s, cudaStream_t st)
+void Ops<TS>::wall(const DevState &s, cudaStream_t st, int block)
 {
     if (s.n_wall == 0) return;
-    k_wall<TS><<<grid_for(s.n_wall, 256), 256, 0, st>>>(s);
+    k_wall<TS><<<grid_for(s.n_wall, block), block, 0, st>>>(s);
 }
 
 template <typename TS>
-void Ops<TS>::fused(const DevState &s, int parity, cudaStream_t st)
+void Ops<TS>::fused(const DevState &s, int parity, cudaStream_t st, int block)
 {
     if (s.n_fluid == 0) return;
-    if (parity) k_fused<TS, 1><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s);
-    else k_fused<TS, 0><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s);
+    if (parity) k_fused<TS, 1><<<grid_for(s.n_fluid, block), block, 0, st>>>(s);
+    else k_fused<TS, 0><<<grid_for(s.n_fluid, block), block, 0, st>>>(s);
+}
+
+template <typename TS>
+void Ops<TS>::dens_batch(const DevState *states, const int2 *map, int nblocks, int parity, int neem, cudaStream_t st,
+                         int block)
+{
+    if (nblocks <= 0) return;
+    if (parity) k_dens_batch<TS, 1><<<nblocks, block, 0, st>>>(states, map, neem);
+    else k_dens_batch<TS, 0><<<nblocks, block, 0, st>>>(states, map, neem);
+}
+
+template <typename TS>
+void Ops<TS>::wall_batch(const DevState *states, const int2 *map, int nblocks, cudaStream_t st, int block)
+{
+    if (nblocks <= 0) return;
+    k_wall_batch<TS><<<nblocks, block, 0, st>>>(states, map);
+}
+
+template <typename TS>
+void Ops<TS>::fused_batch(const DevState *states, const int2 *map, int nblocks, int parity, cudaStream_t st, int block)
+{
+    if (nblocks <= 0) return;
+    if (parity) k_fused_batch<TS, 1><<<nblocks, block, 0, st>>>(states, map);
+    else k_fused_batch<TS, 0><<<nblocks, block, 0, st>>>(states, map);
 }
 
 template <typename TS>

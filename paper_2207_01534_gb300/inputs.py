@@ -264,6 +264,29 @@ def drainage_pack_128(seed_offset=1):
     return solid, r1, r2
 
 
+def batched_sweep(count=64, seed_offset=100):
+    """Parameter points of the batched sweep: ``count`` independent sphere
+    packs, edge n uniform in 48..112, sphere radius uniform in [4, 8], porosity
+    uniform in [0.35, 0.45], viscosity ratio from {1, 5, 10, 50} and contact
+    angle from {30, 60, 90, 120} deg, 6 reservoir slices per end.  Returns one
+    dict per sample; ``batched_sample`` builds its geometry and initial state."""
+    rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_offset))
+    out = []
+    for k in range(count):
+        out.append({"n": int(rng.integers(48, 113)), "radius": float(rng.uniform(4.0, 8.0)),
+                    "porosity": float(rng.uniform(0.35, 0.45)), "M": float(rng.choice([1.0, 5.0, 10.0, 50.0])),
+                    "theta_deg": float(rng.choice([30.0, 60.0, 90.0, 120.0])), "reservoir": 6,
+                    "seed": SEED_BASE + seed_offset + 1 + k})
+    return out
+
+
+def batched_sample(spec):
+    """(solid, rho1, rho2) of one sample of ``batched_sweep``."""
+    solid = sphere_pack(spec["n"], spec["radius"], spec["porosity"], spec["seed"], reservoir=spec["reservoir"])
+    r1, r2 = drainage_init(solid, spec["reservoir"])
+    return solid, r1, r2
+
+
 def random_pops_state(solid, seed, rho_lo=0.02, rho_hi=1.0, noise=0.05):
     """Non-equilibrium populations for parity tests: per-node random component
     densities spread evenly over the 19 directions with a random relative

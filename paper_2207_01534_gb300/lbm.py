@@ -85,9 +85,16 @@ def load(build_if_missing: bool = True):
     lib.lbm_saturation_static.argtypes = [P, P, P, ctypes.c_int64, P, P]
     lib.lbm_last_error.argtypes = [P]
     lib.lbm_last_error.restype = ctypes.c_char_p
+    lib.lbm_create_batch.argtypes = [ctypes.c_int32, ctypes.POINTER(Geometry), ctypes.POINTER(Params),
+                                     ctypes.POINTER(P)]
+    lib.lbm_batch_size.argtypes = [P]
+    lib.lbm_batch_size.restype = ctypes.c_int32
+    lib.lbm_batch_get.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P)]
+    lib.lbm_autotune.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]
     for name in ("lbm_default_params", "lbm_create", "lbm_set_allocator", "lbm_init_densities",
                  "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_step_timed", "lbm_read_fields",
-                 "lbm_saturation", "lbm_saturation_static", "lbm_set_inlet", "lbm_set_stream", "lbm_synchronize", "lbm_get_info"):
+                 "lbm_saturation", "lbm_saturation_static", "lbm_set_inlet", "lbm_set_stream", "lbm_synchronize",
+                 "lbm_get_info", "lbm_create_batch", "lbm_batch_get", "lbm_autotune"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -138,61 +145,94 @@ def saturation_static(rho1_ptr, rho2_ptr, sample_ptr, n, out_ptr, stream=0):
         raise LbmError(code, "lbm_saturation_static")
 
 
+def _geometry_params(lib, solid, tau=(1.0, 1.0), G=3.5, xi=0.0, xi_field=None, periodic=(1, 1, 1), open_axis=-1,
+                     rho_in1=1.0, rho_out2=1.0, body_force=(0.0, 0.0, 0.0), velocity_shift=1, storage="fp32",
+                     kernel="auto", sample=(0, 0), reduce_every=0, drift_limit=1e-6, rho_ref=(0.0, 0.0)):
+    """lbm_geometry and lbm_params of one lattice, plus the arrays they point
+    to (keep them alive until lbm_create returns)."""
+    solid = np.ascontiguousarray(solid, dtype=np.uint8)
+    assert solid.ndim == 3
+    nz, ny, nx = solid.shape
+    g = Geometry()
+    g.nx, g.ny, g.nz = nx, ny, nz
+    g.solid = solid.ctypes.data
+    for a in range(3):
+        g.periodic[a] = int(bool(periodic[a]))
+    g.open_axis = int(open_axis)
+    g.sample_lo, g.sample_hi = int(sample[0]), int(sample[1])
+    xf = None
+    if xi_field is not None:
+        xf = np.ascontiguousarray(xi_field, dtype=np.float32)
+        assert xf.shape == solid.shape
+        g.xi_field = xf.ctypes.data
+    p = Params()
+    lib.lbm_default_params(ctypes.byref(p))
+    p.tau[0], p.tau[1] = float(tau[0]), float(tau[1])
+    p.G = float(G)
+    p.xi = float(xi)
+    p.rho_in1, p.rho_out2 = float(rho_in1), float(rho_out2)
+    for a in range(3):
+        p.body_force[a] = float(body_force[a])
+    p.velocity_shift = int(velocity_shift)
+    p.storage = STORAGE[storage]
+    p.kernel = KERNEL[kernel]
+    p.reduce_every = int(reduce_every)
+    p.drift_limit = float(drift_limit)
+    p.rho_ref[0], p.rho_ref[1] = float(rho_ref[0]), float(rho_ref[1])
+    return g, p, (solid, xf)
+
+
+def _current_stream(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            stream = None
+    return stream
+
+
 class Lattice:
     """One simulation context (``lbm_ctx``) on the current CUDA device."""
 
-    def __init__(self, solid, tau=(1.0, 1.0), G=3.5, xi=0.0, xi_field=None, periodic=(1, 1, 1), open_axis=-1,
-                 rho_in1=1.0, rho_out2=1.0, body_force=(0.0, 0.0, 0.0), velocity_shift=1, storage="fp32",
-                 kernel="auto", sample=(0, 0), reduce_every=0, drift_limit=1e-6, rho_ref=(0.0, 0.0), stream=None):
+    def __init__(self, solid, stream=None, **kw):
         lib = load()
         self._lib = lib
-        solid = np.ascontiguousarray(solid, dtype=np.uint8)
-        assert solid.ndim == 3
-        self.shape = solid.shape
-        nz, ny, nx = solid.shape
-        self.nv = nx * ny * nz
-        g = Geometry()
-        g.nx, g.ny, g.nz = nx, ny, nz
-        g.solid = solid.ctypes.data
-        for a in range(3):
-            g.periodic[a] = int(bool(periodic[a]))
-        g.open_axis = int(open_axis)
-        g.sample_lo, g.sample_hi = int(sample[0]), int(sample[1])
-        xf = None
-        if xi_field is not None:
-            xf = np.ascontiguousarray(xi_field, dtype=np.float32)
-            assert xf.shape == solid.shape
-            g.xi_field = xf.ctypes.data
-        p = Params()
-        lib.lbm_default_params(ctypes.byref(p))
-        p.tau[0], p.tau[1] = float(tau[0]), float(tau[1])
-        p.G = float(G)
-        p.xi = float(xi)
-        p.rho_in1, p.rho_out2 = float(rho_in1), float(rho_out2)
-        for a in range(3):
-            p.body_force[a] = float(body_force[a])
-        p.velocity_shift = int(velocity_shift)
-        p.storage = STORAGE[storage]
-        p.kernel = KERNEL[kernel]
-        p.reduce_every = int(reduce_every)
-        p.drift_limit = float(drift_limit)
-        p.rho_ref[0], p.rho_ref[1] = float(rho_ref[0]), float(rho_ref[1])
+        g, p, keep = _geometry_params(lib, solid, **kw)
+        self.shape = keep[0].shape
+        self.nv = int(np.prod(self.shape))
         h = ctypes.c_void_p()
         _check(lib.lbm_create(ctypes.byref(g), ctypes.byref(p), ctypes.byref(h)))
         self._h = h
-        if stream is None:
-            try:
-                import torch
-
-                if torch.cuda.is_available():
-                    stream = torch.cuda.current_stream().cuda_stream
-            except ImportError:
-                stream = None
+        self._owner = None
+        stream = _current_stream(stream)
         if stream:
             _check(lib.lbm_set_stream(h, ctypes.c_void_p(int(stream))), h)
 
+    @classmethod
+    def _sample(cls, lib, handle, shape, owner):
+        """A sample lattice of a batch (owned by the batch)."""
+        self = cls.__new__(cls)
+        self._lib = lib
+        self._h = handle
+        self._owner = owner
+        self.shape = tuple(shape)
+        self.nv = int(np.prod(self.shape))
+        return self
+
+    def autotune(self, cache_path=None) -> int:
+        """lbm_autotune: pick (or read from the JSON cache) the block size of the split schedule."""
+        b = ctypes.c_int32(0)
+        self._c(self._lib.lbm_autotune(self._h, cache_path.encode() if cache_path else None, ctypes.byref(b)))
+        return int(b.value)
+
     def close(self):
         h = getattr(self, "_h", None)
+        if getattr(self, "_owner", None) is not None:  # a sample: the batch destroys it
+            self._h = None
+            return
         if h is not None and h.value:
             self._lib.lbm_destroy(h)
             self._h = None
@@ -255,3 +295,72 @@ class Lattice:
         i = Info()
         self._c(self._lib.lbm_get_info(self._h, ctypes.byref(i)))
         return {k: getattr(i, k) for k, _ in Info._fields_}
+
+
+class Batch:
+    """Independent lattices stepped together (``lbm_create_batch``): one
+    launch per pass for all samples.  ``samples`` is a list of dicts of
+    Lattice keyword arguments, each with its ``solid``."""
+
+    def __init__(self, samples, stream=None):
+        lib = load()
+        self._lib = lib
+        n = len(samples)
+        gs, ps, keep = (Geometry * n)(), (Params * n)(), []
+        shapes = []
+        for k, kw in enumerate(samples):
+            kw = dict(kw)
+            g, p, kp = _geometry_params(lib, kw.pop("solid"), **kw)
+            gs[k], ps[k] = g, p
+            keep.append(kp)
+            shapes.append(kp[0].shape)
+        h = ctypes.c_void_p()
+        _check(lib.lbm_create_batch(n, gs, ps, ctypes.byref(h)))
+        self._h = h
+        stream = _current_stream(stream)
+        if stream:
+            _check(lib.lbm_set_stream(h, ctypes.c_void_p(int(stream))), h)
+        self.samples = []
+        for k in range(n):
+            sh = ctypes.c_void_p()
+            _check(lib.lbm_batch_get(h, k, ctypes.byref(sh)), h)
+            self.samples.append(Lattice._sample(lib, sh, shapes[k], self))
+
+    def __len__(self):
+        return len(self.samples)
+
+    def __getitem__(self, k):
+        return self.samples[k]
+
+    def _c(self, code):
+        _check(code, self._h)
+
+    def step(self, n: int = 1):
+        self._c(self._lib.lbm_step(self._h, int(n)))
+
+    def synchronize(self):
+        self._c(self._lib.lbm_synchronize(self._h))
+
+    def set_stream(self, stream):
+        self._c(self._lib.lbm_set_stream(self._h, ctypes.c_void_p(int(stream))))
+
+    def autotune(self, cache_path=None) -> int:
+        b = ctypes.c_int32(0)
+        self._c(self._lib.lbm_autotune(self._h, cache_path.encode() if cache_path else None, ctypes.byref(b)))
+        return int(b.value)
+
+    def info(self) -> dict:
+        i = Info()
+        self._c(self._lib.lbm_get_info(self._h, ctypes.byref(i)))
+        return {k: getattr(i, k) for k, _ in Info._fields_}
+
+    def close(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            for smp in self.samples:
+                smp._h = None
+            self._lib.lbm_destroy(h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

@@ -74,3 +74,24 @@ def test_default_params(lib):
     p = lbm.Params()
     assert lib.lbm_default_params(ctypes.byref(p)) == 0
     assert p.G == 3.5 and p.velocity_shift == 1 and tuple(p.tau) == (1.0, 1.0) and p.storage == 0
+
+
+def test_batch_creation_rejects_bad_arguments_before_device_work(lib):
+    from paper_2207_01534_gb300 import lbm
+
+    h = ctypes.c_void_p()
+    g = (lbm.Geometry * 1)()
+    p = (lbm.Params * 1)()
+    assert lib.lbm_create_batch(0, g, p, ctypes.byref(h)) == -1
+    assert lib.lbm_create_batch(1, None, None, ctypes.byref(h)) == -1
+    # an invalid first sample: nothing is created and the message names it
+    solid = np.zeros((6, 6, 6), np.uint8)
+    g[0].nx = g[0].ny = g[0].nz = 6
+    g[0].solid = solid.ctypes.data
+    g[0].periodic[0], g[0].periodic[1], g[0].periodic[2] = 0, 1, 1
+    g[0].open_axis = -1
+    lib.lbm_default_params(ctypes.byref(p[0]))
+    assert lib.lbm_create_batch(1, g, p, ctypes.byref(h)) == -1
+    assert h.value is None
+    assert lib.lbm_last_error(None).decode().startswith("sample 0:")
+    assert lib.lbm_batch_size(None) == 0

@@ -41,6 +41,8 @@ def _load():
     lib.ora_step_count.restype = ctypes.c_long
     lib.ora_fields.argtypes = [ctypes.c_void_p] + [dp] * 6
     lib.ora_saturation.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, dp]
+    lib.ora_record.argtypes = [ctypes.c_void_p, ctypes.c_long]
+    lib.ora_adjoint.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp]
     lib.ora_lattice.argtypes = [ip, dp, ip]
     lib.ora_mirror_map.argtypes = [ctypes.c_int, ip]
     lib.ora_feq.argtypes = [ctypes.c_double, dp, dp]
@@ -176,3 +178,32 @@ class Oracle:
         out = np.zeros(4)
         self._lib.ora_saturation(self._h, int(lo), int(hi), _dp(out))
         return tuple(float(x) for x in out)
+
+    def record(self, n: int) -> None:
+        """Take n steps keeping every state for ``adjoint`` (tiny grids only)."""
+        if self._lib.ora_record(self._h, int(n)) != 0:
+            raise MemoryError("oracle tape")
+
+    def adjoint(self, lo: int = 0, hi: int = 0, seed=None, want_state: bool = False):
+        """Reverse pass over the recorded steps.  J is the smooth non-wetting
+        saturation of the sample slab [lo, hi) (or <seed, f_n> for a seed of
+        shape (2, 19, nz, ny, nx)).  Returns dJ/dxi (nz, ny, nx), dJ/drho_in1
+        and, with want_state, dJ/df_0 and dJ/d(frozen populations)."""
+        gxi = np.zeros(self.shape)
+        grin = np.zeros(1)
+        sd = None
+        if seed is not None:
+            sd = np.ascontiguousarray(seed, dtype=np.float64).reshape(-1)
+            assert sd.size == 2 * 19 * int(np.prod(self.shape))
+        gf = np.zeros((2, 19) + self.shape) if want_state else None
+        gz = np.zeros((2, 19) + self.shape) if want_state else None
+        rc = self._lib.ora_adjoint(self._h, int(lo), int(hi), _dp(sd) if sd is not None else None, _dp(gxi),
+                                   _dp(grin), _dp(gf) if gf is not None else None,
+                                   _dp(gz) if gz is not None else None)
+        if rc != 0:
+            raise RuntimeError("record() first")
+        out = {"xi": gxi, "rho_in1": float(grin[0])}
+        if want_state:
+            out["f"] = gf
+            out["frozen"] = gz
+        return out

@@ -77,6 +77,8 @@ typedef struct ora {
     double *mom[2];    /* sum_i e_i f_i, [3*v + a] */
     double *F[2];      /* total force, [3*v + a] */
     long step;
+    double *tape;      /* recorded states for the adjoint: (tape_len) x [2][Q*nv] */
+    long tape_len;
 } ora_t;
 
 void ora_destroy(ora_t *o);
@@ -277,6 +279,7 @@ void ora_destroy(ora_t *o)
     }
     free(o->solid);
     free(o->xi);
+    free(o->tape);
     free(o);
 }
 
@@ -571,4 +574,355 @@ void ora_saturation(ora_t *o, int lo, int hi, double *out)
     out[1] = cnt > 0 ? smooth / cnt : 0.0;
     out[2] = m1;
     out[3] = m2;
+}
+
+
+/* ===========================================================================
+ * Discrete adjoint of ora_step.
+ *
+ * TEST INFRASTRUCTURE, derived by hand from the seven stages of ora_step (the
+ * paper gives no adjoint).  ora_record takes n steps and keeps every state f_t
+ * (t = 0..n).  ora_adjoint then runs the transposed Jacobian of each step
+ * backwards from the adjoint of the final state, lambda_n = dJ/df_n, where J
+ * is the smooth non-wetting saturation of ora_saturation (or <seed, f_n> when
+ * a seed is given), and accumulates dJ/dxi (per voxel, Eq. 15 chi = 1 +/- xi)
+ * and dJ/drho_in1 (the inlet density of the extrapolation).  Unlike the CUDA
+ * adjoint it works in scatter form on the dense grid: every forward read of a
+ * value becomes an add into that value's adjoint.
+ *
+ * Per step, in reverse order of the forward stages:
+ *   7'. extrapolation: the prescribed component at a plane node xb was
+ *       overwritten, so its adjoint moves to the interior node xI through
+ *       f_eq(rho_b, u_I) + f(xI) - f_eq(rho(xI), u_I), u_I = sum_s m^s / sum_s
+ *       rho^s at xI;
+ *   6'. streaming: each pulled value adds its adjoint to its source (the
+ *       neighbour's post-collision population, the own opposite one at a
+ *       solid, or the frozen value beyond an open plane);
+ *   5'. collision f* = f - (f - f_eq(rho, u)) / tau + (1 - 1/(2 tau)) S(u, F)
+ *       with tau(rho1, rho2) of Eqs. 6-7 and u = sum_s (m^s + F^s/2) / sum_s
+ *       rho^s (Eq. 8; tau cancels there);
+ *   3'. force F^s = -G rho^s A^s + rho^s g, A^s = sum_i w_i e_i psi^sbar(nb_i)
+ *       with the mirrored neighbour beyond an open plane;
+ *   2'. virtual density rho~^s(w) = chi^s(w) N^s(w) / D(w) (Eq. 15);
+ *   1'. moments: rho^s = sum_i f_i^s, m^s = sum_i e_i f_i^s.
+ * ======================================================================== */
+
+static double dfeq_du(int i, int a, double rho, const double u[3])
+{
+    const double e[3] = {(double)EX[i], (double)EY[i], (double)EZ[i]};
+    const double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+    return WT[i] * rho * (e[a] / CS2 + eu * e[a] / (CS2 * CS2) - u[a] / CS2);
+}
+
+static double dsrc_du(int i, int b, const double u[3], const double F[3])
+{
+    const double e[3] = {(double)EX[i], (double)EY[i], (double)EZ[i]};
+    const double eF = e[0] * F[0] + e[1] * F[1] + e[2] * F[2];
+    (void)u;
+    return WT[i] * (-F[b] / CS2 + e[b] * eF / (CS2 * CS2));
+}
+
+static double dsrc_dF(int i, int a, const double u[3])
+{
+    const double e[3] = {(double)EX[i], (double)EY[i], (double)EZ[i]};
+    const double eu = e[0] * u[0] + e[1] * u[1] + e[2] * u[2];
+    return WT[i] * ((e[a] - u[a]) / CS2 + eu * e[a] / (CS2 * CS2));
+}
+
+int ora_record(ora_t *o, long nsteps)
+{
+    const size_t one = (size_t)2 * Q * o->nv;
+    free(o->tape);
+    o->tape = (double *)malloc(sizeof(double) * one * (size_t)(nsteps + 1));
+    if (!o->tape) {
+        o->tape_len = 0;
+        return -1;
+    }
+    o->tape_len = nsteps + 1;
+    for (long t = 0; t <= nsteps; ++t) {
+        if (t > 0) ora_step(o, 1);
+        memcpy(o->tape + one * (size_t)t, o->f[0], sizeof(double) * Q * o->nv);
+        memcpy(o->tape + one * (size_t)t + (size_t)Q * o->nv, o->f[1], sizeof(double) * Q * o->nv);
+    }
+    return 0;
+}
+
+/* Load recorded state t into o->f and recompute the forward intermediates
+ * (moments, virtual densities, forces) of the step that starts from it. */
+static void load_state(ora_t *o, long t)
+{
+    const size_t one = (size_t)2 * Q * o->nv;
+    memcpy(o->f[0], o->tape + one * (size_t)t, sizeof(double) * Q * o->nv);
+    memcpy(o->f[1], o->tape + one * (size_t)t + (size_t)Q * o->nv, sizeof(double) * Q * o->nv);
+    compute_moments(o);
+    compute_virtual_density(o);
+    compute_forces(o);
+}
+
+/* 7': adjoint of neem_plane for one plane.  lam is [2][Q*nv]; fn is the
+ * post-stream state (the interior node is never overwritten, so the recorded
+ * next state holds the values the extrapolation read). */
+static void neem_adjoint(const ora_t *o, double *lam[2], const double *fn[2], int plane, int comp, double rho_b,
+                         int inward, double *g_rho_b)
+{
+    const int ax = o->open_axis;
+    const long nv = o->nv;
+    const int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
+    for (int p2 = 0; p2 < o->n[a2]; ++p2) {
+        for (int p1 = 0; p1 < o->n[a1]; ++p1) {
+            int c[3];
+            c[ax] = plane;
+            c[a1] = p1;
+            c[a2] = p2;
+            const long xb = vid(o, c);
+            if (o->solid[xb]) continue;
+            c[ax] = plane + inward;
+            const long xi = vid(o, c);
+            double r[2] = {0, 0}, m[3] = {0, 0, 0};
+            for (int s = 0; s < 2; ++s)
+                for (int i = 0; i < Q; ++i) {
+                    const double fi = fn[s][i * nv + xi];
+                    r[s] += fi;
+                    m[0] += EX[i] * fi;
+                    m[1] += EY[i] * fi;
+                    m[2] += EZ[i] * fi;
+                }
+            const double R = r[0] + r[1];
+            const double u[3] = {m[0] / R, m[1] / R, m[2] / R};
+            double rbar = 0, ubar[3] = {0, 0, 0}, gb = 0;
+            for (int i = 0; i < Q; ++i) {
+                const double mu = lam[comp][i * nv + xb];
+                lam[comp][i * nv + xb] = 0.0;  /* overwritten: no dependence on the old value */
+                lam[comp][i * nv + xi] += mu;  /* the f(xI) term */
+                const double feq1 = feq_i(i, 1.0, u);
+                gb += mu * feq1;       /* d f_eq(rho_b, u) / d rho_b */
+                rbar -= mu * feq1;     /* - d f_eq(rho(xI), u) / d rho(xI) */
+                for (int a = 0; a < 3; ++a) ubar[a] += mu * (dfeq_du(i, a, rho_b, u) - dfeq_du(i, a, r[comp], u));
+            }
+            for (int j = 0; j < Q; ++j) {
+                lam[comp][j * nv + xi] += rbar;
+                const double e[3] = {(double)EX[j], (double)EY[j], (double)EZ[j]};
+                double du = 0;
+                for (int a = 0; a < 3; ++a) du += ubar[a] * (e[a] - u[a]) / R;
+                lam[0][j * nv + xi] += du;
+                lam[1][j * nv + xi] += du;
+            }
+            if (g_rho_b) *g_rho_b += gb;
+        }
+    }
+}
+
+int ora_adjoint(ora_t *o, int lo, int hi, const double *seed, double *grad_xi, double *grad_rho_in1,
+                double *grad_f, double *grad_frozen)
+{
+    if (!o->tape || o->tape_len < 1) return -1;
+    const long nv = o->nv, n = o->tape_len - 1;
+    const size_t one = (size_t)Q * nv;
+    double *lam[2], *lamS[2], *gfz[2], *psib[2], *rhob[2];
+    for (int s = 0; s < 2; ++s) {
+        lam[s] = (double *)calloc(one, sizeof(double));
+        lamS[s] = (double *)calloc(one, sizeof(double));
+        gfz[s] = (double *)calloc(one, sizeof(double));
+        psib[s] = (double *)calloc((size_t)nv, sizeof(double));
+        rhob[s] = (double *)calloc((size_t)nv, sizeof(double));
+    }
+    double *gxi = (double *)calloc((size_t)nv, sizeof(double));
+    double grin = 0.0;
+
+    /* adjoint of the final state */
+    if (seed) {
+        memcpy(lam[0], seed, sizeof(double) * one);
+        memcpy(lam[1], seed + one, sizeof(double) * one);
+    } else {
+        const double *fT[2] = {o->tape + 2 * one * (size_t)n, o->tape + 2 * one * (size_t)n + one};
+        double cnt = 0;
+        for (long v = 0; v < nv; ++v) {
+            if (o->solid[v]) continue;
+            int in = 1;
+            if (o->open_axis >= 0 && hi > lo) {
+                int c[3];
+                coords(o, v, c);
+                in = (c[o->open_axis] >= lo && c[o->open_axis] < hi);
+            }
+            cnt += in;
+        }
+        for (long v = 0; v < nv; ++v) {
+            if (o->solid[v] || cnt == 0) continue;
+            if (o->open_axis >= 0 && hi > lo) {
+                int c[3];
+                coords(o, v, c);
+                if (c[o->open_axis] < lo || c[o->open_axis] >= hi) continue;
+            }
+            double r[2] = {0, 0};
+            for (int s = 0; s < 2; ++s)
+                for (int i = 0; i < Q; ++i) r[s] += fT[s][i * nv + v];
+            const double R = r[0] + r[1];
+            /* d/d rho1 of rho1/(rho1+rho2) = rho2/R^2, d/d rho2 = -rho1/R^2 */
+            for (int i = 0; i < Q; ++i) {
+                lam[0][i * nv + v] = r[1] / (R * R) / cnt;
+                lam[1][i * nv + v] = -r[0] / (R * R) / cnt;
+            }
+        }
+    }
+
+    const double nu[2] = {CS2 * (o->tau[0] - 0.5), CS2 * (o->tau[1] - 0.5)};
+    for (long t = n - 1; t >= 0; --t) {
+        load_state(o, t);
+        const double *fn[2] = {o->tape + 2 * one * (size_t)(t + 1), o->tape + 2 * one * (size_t)(t + 1) + one};
+        /* 7' (outlet was extrapolated last, so it is undone first) */
+        if (o->open_axis >= 0) {
+            neem_adjoint(o, lam, fn, o->n[o->open_axis] - 1, 1, o->rho_out2, -1, NULL);
+            neem_adjoint(o, lam, fn, 0, 0, o->rho_in1, +1, &grin);
+        }
+        /* 6' streaming, scatter form */
+        for (int s = 0; s < 2; ++s) memset(lamS[s], 0, sizeof(double) * one);
+        for (long v = 0; v < nv; ++v) {
+            if (o->solid[v]) continue;
+            int c[3];
+            coords(o, v, c);
+            for (int s = 0; s < 2; ++s) {
+                lamS[s][v] += lam[s][v];
+                for (int i = 1; i < Q; ++i) {
+                    long src;
+                    const double l = lam[s][i * nv + v];
+                    if (neighbour(o, c, -EX[i], -EY[i], -EZ[i], &src))
+                        gfz[s][i * nv + v] += l;
+                    else if (o->solid[src])
+                        lamS[s][o->opp[i] * nv + v] += l;
+                    else
+                        lamS[s][i * nv + src] += l;
+                }
+            }
+        }
+        /* 5', 3' local part, 1' (written into lam, the adjoint of state t) */
+        for (int s = 0; s < 2; ++s) {
+            memset(psib[s], 0, sizeof(double) * (size_t)nv);
+            memset(rhob[s], 0, sizeof(double) * (size_t)nv);
+        }
+        for (long v = 0; v < nv; ++v) {
+            if (o->solid[v]) {
+                for (int s = 0; s < 2; ++s)
+                    for (int i = 0; i < Q; ++i) lam[s][i * nv + v] = 0.0;
+                continue;
+            }
+            int c[3];
+            coords(o, v, c);
+            const double r[2] = {o->rho[0][v], o->rho[1][v]};
+            const double R = r[0] + r[1];
+            double tau_s, u[3];
+            relaxation_and_velocity(o, v, &tau_s, u);
+            const double cf = 1.0 - 1.0 / (2.0 * tau_s);
+            double rb[2] = {0, 0}, ub[3] = {0, 0, 0}, Fb[2][3] = {{0, 0, 0}, {0, 0, 0}}, mb[2][3], taub = 0;
+            for (int s = 0; s < 2; ++s) {
+                const double *F = &o->F[s][3 * v];
+                for (int i = 0; i < Q; ++i) {
+                    const double L = lamS[s][i * nv + v];
+                    const double fi = o->f[s][i * nv + v];
+                    const double fe = feq_i(i, r[s], u);
+                    const double S = src_i(i, u, F);
+                    rb[s] += L * feq_i(i, 1.0, u) / tau_s;
+                    for (int a = 0; a < 3; ++a) {
+                        ub[a] += L * (dfeq_du(i, a, r[s], u) / tau_s + cf * dsrc_du(i, a, u, F));
+                        Fb[s][a] += L * cf * dsrc_dF(i, a, u);
+                    }
+                    taub += L * ((fi - fe) / (tau_s * tau_s) + S / (2.0 * tau_s * tau_s));
+                }
+            }
+            /* tau(rho1, rho2), Eqs. 6-7 */
+            rb[0] += taub * r[1] * (nu[0] - nu[1]) / (R * R * CS2);
+            rb[1] += taub * r[0] * (nu[1] - nu[0]) / (R * R * CS2);
+            /* u = sum_s (m^s + shift F^s / 2) / R */
+            for (int s = 0; s < 2; ++s) {
+                for (int a = 0; a < 3; ++a) {
+                    mb[s][a] = ub[a] / R;
+                    if (o->velocity_shift) Fb[s][a] += 0.5 * ub[a] / R;
+                    rb[s] -= ub[a] * u[a] / R;
+                }
+            }
+            /* F^s = -G rho^s A^s + rho^s g */
+            for (int s = 0; s < 2; ++s) {
+                const int sb = 1 - s;
+                double A[3] = {0, 0, 0};
+                long nbs[Q];
+                for (int i = 1; i < Q; ++i) {
+                    long nb;
+                    nbs[i] = -1;
+                    if (neighbour(o, c, EX[i], EY[i], EZ[i], &nb)) {
+                        const int j = o->mirror[i];
+                        if (neighbour(o, c, EX[j], EY[j], EZ[j], &nb)) continue; /* cannot happen */
+                    }
+                    nbs[i] = nb;
+                    A[0] += WT[i] * o->rho[sb][nb] * EX[i];
+                    A[1] += WT[i] * o->rho[sb][nb] * EY[i];
+                    A[2] += WT[i] * o->rho[sb][nb] * EZ[i];
+                }
+                double Ab[3];
+                for (int a = 0; a < 3; ++a) {
+                    rb[s] += Fb[s][a] * (-o->G * A[a] + o->g[a]);
+                    Ab[a] = -o->G * r[s] * Fb[s][a];
+                }
+                for (int i = 1; i < Q; ++i)
+                    if (nbs[i] >= 0) psib[sb][nbs[i]] += WT[i] * (EX[i] * Ab[0] + EY[i] * Ab[1] + EZ[i] * Ab[2]);
+            }
+            /* pre-collision populations: direct term and moments */
+            for (int s = 0; s < 2; ++s)
+                for (int i = 0; i < Q; ++i)
+                    lam[s][i * nv + v] = (1.0 - 1.0 / tau_s) * lamS[s][i * nv + v] + rb[s] +
+                                         EX[i] * mb[s][0] + EY[i] * mb[s][1] + EZ[i] * mb[s][2];
+        }
+        /* 2': psi adjoint of a solid is that of its virtual density */
+        for (long v = 0; v < nv; ++v) {
+            if (!o->solid[v]) {
+                for (int s = 0; s < 2; ++s) rhob[s][v] += psib[s][v];
+                continue;
+            }
+            if (psib[0][v] == 0.0 && psib[1][v] == 0.0) continue;
+            int c[3];
+            coords(o, v, c);
+            double num[2] = {0, 0}, den = 0;
+            for (int i = 1; i < Q; ++i) {
+                long nb;
+                if (neighbour(o, c, EX[i], EY[i], EZ[i], &nb) || o->solid[nb]) continue;
+                num[0] += WT[i] * o->rho[0][nb];
+                num[1] += WT[i] * o->rho[1][nb];
+                den += WT[i];
+            }
+            if (den <= 0) continue;
+            const double chi[2] = {1.0 + o->xi[v], 1.0 - o->xi[v]};
+            gxi[v] += psib[0][v] * num[0] / den - psib[1][v] * num[1] / den;
+            for (int i = 1; i < Q; ++i) {
+                long nb;
+                if (neighbour(o, c, EX[i], EY[i], EZ[i], &nb) || o->solid[nb]) continue;
+                for (int s = 0; s < 2; ++s) rhob[s][nb] += psib[s][v] * chi[s] * WT[i] / den;
+            }
+        }
+        /* 1' for the non-local density adjoints */
+        for (long v = 0; v < nv; ++v) {
+            if (o->solid[v]) continue;
+            for (int s = 0; s < 2; ++s)
+                for (int i = 0; i < Q; ++i) lam[s][i * nv + v] += rhob[s][v];
+        }
+    }
+    /* leave the oracle at the final recorded state */
+    load_state(o, n);
+
+    if (grad_xi) memcpy(grad_xi, gxi, sizeof(double) * (size_t)nv);
+    if (grad_rho_in1) *grad_rho_in1 = grin;
+    if (grad_f) {
+        memcpy(grad_f, lam[0], sizeof(double) * one);
+        memcpy(grad_f + one, lam[1], sizeof(double) * one);
+    }
+    if (grad_frozen) {
+        memcpy(grad_frozen, gfz[0], sizeof(double) * one);
+        memcpy(grad_frozen + one, gfz[1], sizeof(double) * one);
+    }
+    for (int s = 0; s < 2; ++s) {
+        free(lam[s]);
+        free(lamS[s]);
+        free(gfz[s]);
+        free(psib[s]);
+        free(rhob[s]);
+    }
+    free(gxi);
+    return 0;
 }

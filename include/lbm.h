@@ -236,6 +236,34 @@ lbm_status lbm_batch_get(lbm_ctx *batch, int32_t k, lbm_ctx **sample);
  * and is returned as is.  Synchronises. */
 lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t *block_out);
 
+/* ---- Reverse pass (gradients) -------------------------------------------
+ * Gradients of J = the smooth non-wetting saturation of the sample slab
+ * (out[1] of lbm_saturation) after n steps, with respect to the per-voxel
+ * wettability xi (chi^(1,2) = 1 +/- xi in the virtual wall density, Eq. 15)
+ * and the inlet density rho_in1 of the open-boundary extrapolation (Section
+ * 2).  The paper has no adjoint; this is the exact discrete adjoint of the
+ * step as implemented (FP32 or FP64 storage, split schedule, single lattice;
+ * LBM_ERR_UNSUPPORTED otherwise).
+ *
+ * lbm_set_xi_field sets xi on every wall voxel from a dense nx*ny*nz float
+ * array (host pointer when on_device = 0, device pointer otherwise); values
+ * at non-wall voxels are ignored.
+ *
+ * lbm_record takes nsteps steps like lbm_step and keeps a copy of the state
+ * every `every` steps (checkpoints: ceil(nsteps/every) + 1 copies of the
+ * populations).  lbm_adjoint then computes the loss J of the final state and
+ * runs the reverse pass: each segment of `every` steps is recomputed from its
+ * checkpoint (keeping its every - 1 intermediate states), then reversed.
+ * Outputs: grad_xi (device pointer to nx*ny*nz floats, or NULL) receives
+ * dloss * dJ/dxi on wall voxels and 0 elsewhere; *grad_rho_in1 (host, or
+ * NULL) receives dloss * dJ/drho_in1 (0 without open planes); *loss (host, or
+ * NULL) receives J.  The context is left at the recorded final state, and the
+ * recording stays usable until the state or a parameter changes (lbm_step,
+ * initialisation, lbm_set_inlet, lbm_set_xi_field).  Synchronises. */
+lbm_status lbm_set_xi_field(lbm_ctx *ctx, const float *xi, int32_t on_device);
+lbm_status lbm_record(lbm_ctx *ctx, int64_t nsteps, int32_t every);
+lbm_status lbm_adjoint(lbm_ctx *ctx, double dloss, float *grad_xi, double *grad_rho_in1, double *loss);
+
 /* Largest n accepted by lbm_saturation_static. */
 #define LBM_SATURATION_STATIC_MAX_N 16777216
 

@@ -14,6 +14,13 @@
 #include "lbm.h"
 #include "lbm_internal.h"
 #include "lbm_kernels.cuh"
+#include "lbm_adjoint.cuh"
+
+namespace lbm {
+// instantiated in lbm_adj32.cu / lbm_adj64.cu
+extern template struct Adj<float>;
+extern template struct Adj<double>;
+}
 
 using namespace lbm;
 
@@ -71,6 +78,18 @@ struct lbm_ctx {
     int64_t graph_launches = 0;  // kernels per replay
     size_t f_bytes = 0, rest_bytes = 0, bc_bytes = 0;  // the state a step reads and writes
     std::vector<uint8_t> solid_host;  // the mask, for host-side statistics
+    // recording for the reverse pass (lbm_record / lbm_adjoint)
+    struct Record {
+        bool valid = false;
+        int64_t step0 = 0, n = 0, every = 0, step_end = 0;
+        std::vector<void *> ckpt;  // state at step0 + k*every
+        void *final_state = nullptr;
+        std::vector<void *> seg;   // states inside one segment
+        void *lam[2] = {nullptr, nullptr}, *rb[2] = {nullptr, nullptr};
+        void *abar = nullptr, *wbar = nullptr, *psi = nullptr;
+        double *gxi = nullptr, *grin = nullptr;
+        int64_t count = 0;  // fluid nodes of the sample slab
+    } rec;
     void *psi_alt = nullptr;
     int pipe_grid = 0;
     int64_t pipe_launches = 0;
@@ -230,6 +249,7 @@ lbm_status device_status(lbm_ctx *c)
 void touch(lbm_ctx *c)
 {
     c->graph_dirty = true;
+    c->rec.valid = false;
     if (c->parent) {
         c->parent->states_dirty = true;
         c->parent->graph_dirty = true;
@@ -434,6 +454,8 @@ lbm_status ensure_graph(lbm_ctx *c)
     return LBM_OK;
 }
 
+void free_record(lbm_ctx *c);
+
 void destroy_ctx(lbm_ctx *c)
 {
     if (!c) return;
@@ -442,6 +464,7 @@ void destroy_ctx(lbm_ctx *c)
     for (lbm_ctx *q : c->subs) destroy_ctx(q);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    free_record(c);
     std::vector<std::pair<void *, size_t>> a = c->allocs;
     for (auto &q : a) dfree(c, q.first);
     if (c->h_flag) cudaFreeHost(c->h_flag);
@@ -609,6 +632,81 @@ lbm_status tune(lbm_ctx *c, int *best)
     if (st == LBM_OK && e != cudaSuccess) st = cuda_fail(c, e, "lbm_autotune: restore");
     if (st != LBM_OK) apply_block(c, block0);
     return st;
+}
+
+// ---- recording and reverse pass ------------------------------------------
+size_t state_bytes(const lbm_ctx *c) { return c->f_bytes + c->rest_bytes + c->bc_bytes; }
+
+// Copy the live state (post-stream, with the pending open-plane extrapolation
+// applied: it is idempotent) into buf.
+void snap_save(lbm_ctx *c, void *buf)
+{
+    if (c->step > 0)
+        dispatch(c, [&](auto tag) { Ops<decltype(tag)>::plane(c->s, (int)(c->step & 1), c->stream); });
+    char *b = (char *)buf;
+    cudaMemcpyAsync(b, c->s.f, c->f_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(b + c->f_bytes, c->s.rest, c->rest_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (c->bc_bytes)
+        cudaMemcpyAsync(b + c->f_bytes + c->rest_bytes, c->s.bc, c->bc_bytes, cudaMemcpyDeviceToDevice, c->stream);
+}
+
+void snap_load(lbm_ctx *c, const void *buf)
+{
+    const char *b = (const char *)buf;
+    cudaMemcpyAsync(c->s.f, b, c->f_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    cudaMemcpyAsync(c->s.rest, b + c->f_bytes, c->rest_bytes, cudaMemcpyDeviceToDevice, c->stream);
+    if (c->bc_bytes)
+        cudaMemcpyAsync(c->s.bc, b + c->f_bytes + c->rest_bytes, c->bc_bytes, cudaMemcpyDeviceToDevice, c->stream);
+}
+
+// The lattice with its populations read from a saved state and psi in psi_buf.
+DevState snap_state(const lbm_ctx *c, void *buf, void *psi_buf)
+{
+    DevState s = c->s;
+    char *b = (char *)buf;
+    s.f = b;
+    s.rest = b + c->f_bytes;
+    if (c->bc_bytes) s.bc = b + c->f_bytes + c->rest_bytes;
+    s.psi = psi_buf;
+    return s;
+}
+
+void free_record(lbm_ctx *c)
+{
+    auto &r = c->rec;
+    for (void *q : r.ckpt) dfree(c, q);
+    for (void *q : r.seg) dfree(c, q);
+    r.ckpt.clear();
+    r.seg.clear();
+    for (void **q : {&r.final_state, &r.lam[0], &r.lam[1], &r.rb[0], &r.rb[1], &r.abar, &r.wbar, &r.psi})
+        if (*q) {
+            dfree(c, *q);
+            *q = nullptr;
+        }
+    if (r.gxi) dfree(c, r.gxi);
+    if (r.grin) dfree(c, r.grin);
+    r.gxi = r.grin = nullptr;
+    r.valid = false;
+}
+
+bool adjoint_supported(const lbm_ctx *c)
+{
+    return c->subs.empty() && !c->parent && c->kernel != LBM_KERNEL_FUSED &&
+           (c->storage == LBM_STORE_FP32 || c->storage == LBM_STORE_FP64);
+}
+
+template <class Fn>
+void dispatch_adj(const lbm_ctx *c, Fn &&fn)
+{
+    if (c->storage == LBM_STORE_FP64) fn(double{});
+    else fn(float{});
+}
+
+template <typename C>
+__global__ void k_set_wxi(const uint32_t *wpvox, int n_wall, const float *xi, C *wxi)
+{
+    const int w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w < n_wall) wxi[w] = (C)xi[wpvox[w]];
 }
 
 }  // namespace
@@ -1059,6 +1157,7 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f)
 lbm_status lbm_step(lbm_ctx *c, int64_t n)
 {
     if (!c || n < 0) return LBM_ERR_ARG;
+    if (n > 0) c->rec.valid = false;
     if (c->parent) return fail(c, LBM_ERR_ARG, "a sample of a batch is stepped through its batch");
     if (!c->subs.empty()) {
         for (lbm_ctx *q : c->subs)
@@ -1313,6 +1412,194 @@ lbm_status lbm_autotune(lbm_ctx *c, const char *cache_path, int32_t *block_out)
         if (!write_cache(cache_path, kv)) return fail(c, LBM_ERR_ARG, "lbm_autotune: cannot write the cache file");
     }
     return LBM_OK;
+}
+
+lbm_status lbm_set_xi_field(lbm_ctx *c, const float *xi, int32_t on_device)
+{
+    if (!c || !xi) return LBM_ERR_ARG;
+    if (!c->subs.empty()) return no_batch(c, "lbm_set_xi_field");
+    if (c->s.n_wall == 0) return LBM_OK;
+    const float *src = xi;
+    float *tmp = nullptr;
+    cudaError_t e = cudaSuccess;
+    if (!on_device) {
+        tmp = (float *)dalloc(c, (size_t)c->nv * 4);
+        if (!tmp) return fail(c, LBM_ERR_ALLOC, "temporary xi buffer");
+        e = cudaMemcpyAsync(tmp, xi, (size_t)c->nv * 4, cudaMemcpyHostToDevice, c->stream);
+        src = tmp;
+    }
+    const int g = (c->s.n_wall + 255) / 256;
+    if (e == cudaSuccess) {
+        if (c->storage == LBM_STORE_FP64)
+            k_set_wxi<double><<<g, 256, 0, c->stream>>>(c->s.wpvox, c->s.n_wall, src, (double *)c->s.wxi);
+        else
+            k_set_wxi<float><<<g, 256, 0, c->stream>>>(c->s.wpvox, c->s.n_wall, src, (float *)c->s.wxi);
+        c->launches += 1;
+    }
+    if (tmp) {
+        cudaStreamSynchronize(c->stream);
+        dfree(c, tmp);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_xi_field");
+    touch(c);
+    return check_launch(c, "lbm_set_xi_field");
+}
+
+lbm_status lbm_record(lbm_ctx *c, int64_t nsteps, int32_t every)
+{
+    if (!c || nsteps < 1 || every < 1) return LBM_ERR_ARG;
+    if (!adjoint_supported(c))
+        return fail(c, LBM_ERR_UNSUPPORTED, "the reverse pass needs a single lattice with FP32 or FP64 storage and "
+                                            "the split schedule");
+    auto &r = c->rec;
+    const int64_t nck = (nsteps + every - 1) / every;
+    const size_t sb = state_bytes(c);
+    if ((int64_t)r.ckpt.size() != nck || r.every != every) {
+        free_record(c);
+        for (int64_t k = 0; k < nck; ++k) {
+            void *q = dalloc(c, sb);
+            if (!q) {
+                free_record(c);
+                return fail(c, LBM_ERR_ALLOC, "lbm_record: checkpoints");
+            }
+            r.ckpt.push_back(q);
+        }
+        r.final_state = dalloc(c, sb);
+        if (!r.final_state) {
+            free_record(c);
+            return fail(c, LBM_ERR_ALLOC, "lbm_record: final state");
+        }
+    }
+    r.step0 = c->step;
+    r.n = nsteps;
+    r.every = every;
+    for (int64_t k = 0; k < nck; ++k) {
+        snap_save(c, r.ckpt[(size_t)k]);
+        const int64_t len = std::min<int64_t>(every, nsteps - k * every);
+        lbm_status st = lbm_step(c, len);
+        if (st != LBM_OK) return st;
+    }
+    snap_save(c, r.final_state);
+    r.step_end = c->step;
+    lbm_status st = check_launch(c, "lbm_record");
+    if (st != LBM_OK) return st;
+    r.valid = true;
+    return device_status(c);
+}
+
+lbm_status lbm_adjoint(lbm_ctx *c, double dloss, float *grad_xi, double *grad_rho_in1, double *loss)
+{
+    if (!c) return LBM_ERR_ARG;
+    auto &r = c->rec;
+    if (!r.valid || c->step != r.step_end)
+        return fail(c, LBM_ERR_ARG, "lbm_adjoint needs a recording (lbm_record) that is still current");
+    const size_t sb = state_bytes(c);
+    const size_t csz = c->storage == LBM_STORE_FP64 ? 16 : 8;  // compute-type pair
+    const int64_t npad = c->s.npad, nv = c->nv;
+    // reverse-pass buffers (kept for later calls)
+    while ((int64_t)r.seg.size() < r.every - 1) {
+        void *q = dalloc(c, sb);
+        if (!q) return fail(c, LBM_ERR_ALLOC, "lbm_adjoint: segment states");
+        r.seg.push_back(q);
+    }
+    auto need = [&](void *&q, size_t bytes) {
+        if (!q) q = dalloc(c, bytes);
+        return q != nullptr;
+    };
+    if (!need(r.lam[0], (size_t)19 * npad * csz) || !need(r.lam[1], (size_t)19 * npad * csz) ||
+        !need(r.rb[0], (size_t)nv * csz) || !need(r.rb[1], (size_t)nv * csz) || !need(r.abar, (size_t)3 * nv * csz) ||
+        !need(r.wbar, (size_t)nv * csz) || !need(r.psi, (size_t)nv * csz))
+        return fail(c, LBM_ERR_ALLOC, "lbm_adjoint: adjoint buffers");
+    if (!r.gxi) r.gxi = (double *)dalloc(c, (size_t)std::max(1, c->s.n_wall) * 8);
+    if (!r.grin) r.grin = (double *)dalloc(c, (size_t)std::max(1, c->s.nxy) * 8);
+    if (!r.gxi || !r.grin) return fail(c, LBM_ERR_ALLOC, "lbm_adjoint: gradient accumulators");
+    cudaStream_t st = c->stream;
+
+    // loss of the final state (its densities land in the live psi)
+    run_reduce(c);
+    double red[kReduceSlots];
+    cudaError_t e = cudaMemcpyAsync(red, c->d_red, sizeof(red), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_adjoint: loss");
+    const double count = red[2];
+    const double J = count > 0 ? red[4] / count : 0.0;
+
+    AdjState a{};
+    a.lam_in = r.lam[0];
+    a.lam_out = r.lam[1];
+    a.rb_in = r.rb[0];
+    a.rb_out = r.rb[1];
+    a.abar = r.abar;
+    a.wbar = r.wbar;
+    a.gxi = r.gxi;
+    a.grin = r.grin;
+    cudaMemsetAsync(a.lam_in, 0, (size_t)19 * npad * csz, st);
+    cudaMemsetAsync(a.rb_in, 0, (size_t)nv * csz, st);
+    cudaMemsetAsync(a.abar, 0, (size_t)3 * nv * csz, st);
+    cudaMemsetAsync(a.wbar, 0, (size_t)nv * csz, st);
+    cudaMemsetAsync(a.gxi, 0, (size_t)std::max(1, c->s.n_wall) * 8, st);
+    cudaMemsetAsync(a.grin, 0, (size_t)std::max(1, c->s.nxy) * 8, st);
+    dispatch_adj(c, [&](auto tag) {
+        using TS = decltype(tag);
+        Adj<TS>::seed(c->s, a, count > 0 ? 1.0 / count : 0.0, st);
+    });
+    c->launches += 1;
+
+    const int64_t nck = (int64_t)r.ckpt.size();
+    for (int64_t k = nck - 1; k >= 0; --k) {
+        const int64_t t0 = k * r.every;
+        const int64_t len = std::min<int64_t>(r.every, r.n - t0);
+        // recompute the segment from its checkpoint
+        snap_load(c, r.ckpt[(size_t)k]);
+        c->step = r.step0 + t0;
+        std::vector<void *> S((size_t)len + 1);
+        S[0] = r.ckpt[(size_t)k];
+        S[(size_t)len] = k + 1 < nck ? r.ckpt[(size_t)k + 1] : r.final_state;
+        for (int64_t q = 1; q < len; ++q) {
+            enqueue_step(c, nullptr);
+            S[(size_t)q] = r.seg[(size_t)q - 1];
+            snap_save(c, S[(size_t)q]);
+        }
+        // reverse the segment's steps
+        for (int64_t q = len - 1; q >= 0; --q) {
+            const int par = (int)((r.step0 + t0 + q) & 1);
+            const DevState s_t = snap_state(c, S[(size_t)q], r.psi);
+            const DevState s_n = snap_state(c, S[(size_t)q + 1], r.psi);
+            dispatch_adj(c, [&](auto tag) {
+                using TS = decltype(tag);
+                Ops<TS>::dens(s_t, par, 0, st);
+                Ops<TS>::wall(s_t, st);
+                Adj<TS>::plane(s_n, a, 1 - par, 1, st);  // outlet (extrapolated last)
+                Adj<TS>::plane(s_n, a, 1 - par, 0, st);  // inlet
+                Adj<TS>::node(s_t, a, par, st);
+                Adj<TS>::wall(s_t, a, st);
+                Adj<TS>::dens(s_t, a, st);
+            });
+            c->launches += 7;
+            std::swap(a.lam_in, a.lam_out);
+            std::swap(a.rb_in, a.rb_out);
+        }
+    }
+    // back to the recorded final state
+    snap_load(c, r.final_state);
+    c->step = r.step_end;
+    lbm_status stt = check_launch(c, "lbm_adjoint");
+    if (stt != LBM_OK) return stt;
+    if (grad_xi) {
+        cudaMemsetAsync(grad_xi, 0, (size_t)nv * 4, st);
+        dispatch_adj(c, [&](auto tag) { Adj<decltype(tag)>::xi_out(c->s, a, dloss, grad_xi, st); });
+        c->launches += 1;
+    }
+    std::vector<double> gr((size_t)std::max(1, c->s.nxy), 0.0);
+    e = cudaMemcpyAsync(gr.data(), a.grin, gr.size() * 8, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_adjoint");
+    double g = 0.0;
+    for (double v : gr) g += v;  // fixed order
+    if (grad_rho_in1) *grad_rho_in1 = c->s.open_z ? g * dloss : 0.0;
+    if (loss) *loss = J;
+    stt = check_launch(c, "lbm_adjoint");
+    return stt != LBM_OK ? stt : device_status(c);
 }
 
 const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }

@@ -91,10 +91,15 @@ def load(build_if_missing: bool = True):
     lib.lbm_batch_size.restype = ctypes.c_int32
     lib.lbm_batch_get.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P)]
     lib.lbm_autotune.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]
+    lib.lbm_set_xi_field.argtypes = [P, P, ctypes.c_int32]
+    lib.lbm_record.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
+    lib.lbm_adjoint.argtypes = [P, ctypes.c_double, P, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_double)]
     for name in ("lbm_default_params", "lbm_create", "lbm_set_allocator", "lbm_init_densities",
                  "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_step_timed", "lbm_read_fields",
                  "lbm_saturation", "lbm_saturation_static", "lbm_set_inlet", "lbm_set_stream", "lbm_synchronize",
-                 "lbm_get_info", "lbm_create_batch", "lbm_batch_get", "lbm_autotune"):
+                 "lbm_get_info", "lbm_create_batch", "lbm_batch_get", "lbm_autotune", "lbm_set_xi_field",
+                 "lbm_record", "lbm_adjoint"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -221,6 +226,33 @@ class Lattice:
         self.shape = tuple(shape)
         self.nv = int(np.prod(self.shape))
         return self
+
+    def set_xi_field(self, xi):
+        """Wettability xi per voxel (Eq. 15): a numpy array or a CUDA float32 tensor of the grid's shape."""
+        if hasattr(xi, "data_ptr"):
+            import torch
+
+            assert xi.is_cuda and xi.dtype == torch.float32 and xi.is_contiguous() and tuple(xi.shape) == self.shape
+            self._c(self._lib.lbm_set_xi_field(self._h, ctypes.c_void_p(xi.data_ptr()), 1))
+        else:
+            a = np.ascontiguousarray(np.broadcast_to(xi, self.shape), dtype=np.float32)
+            self._c(self._lib.lbm_set_xi_field(self._h, a.ctypes.data, 0))
+
+    def record(self, nsteps: int, every: int = 50):
+        """lbm_record: nsteps steps, keeping a checkpoint every ``every`` steps."""
+        self._c(self._lib.lbm_record(self._h, int(nsteps), int(every)))
+
+    def adjoint(self, dloss: float = 1.0, grad_xi=None):
+        """lbm_adjoint: reverse pass of the recording.  ``grad_xi`` (optional)
+        is a CUDA float32 tensor of the grid's shape that receives dloss *
+        dJ/dxi.  Returns (J, dloss * dJ/drho_in1)."""
+        gr, J = ctypes.c_double(0.0), ctypes.c_double(0.0)
+        ptr = None
+        if grad_xi is not None:
+            assert grad_xi.is_cuda and grad_xi.is_contiguous() and tuple(grad_xi.shape) == self.shape
+            ptr = ctypes.c_void_p(grad_xi.data_ptr())
+        self._c(self._lib.lbm_adjoint(self._h, float(dloss), ptr, ctypes.byref(gr), ctypes.byref(J)))
+        return J.value, gr.value
 
     def autotune(self, cache_path=None) -> int:
         """lbm_autotune: pick (or read from the JSON cache) the block size of the split schedule."""

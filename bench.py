@@ -12,6 +12,12 @@ nodes; the all-voxel rate is in ``config``).
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 For N > 1 run under torchrun: every rank runs an independent replica.
 
+``--workload adjoint_pack_96`` times the reverse pass: a 96^3 sphere pack
+(radius 6, porosity 0.40), 500 steps of imbibition in FP32, loss = smooth
+non-wetting saturation, gradients with respect to the per-voxel wettability
+and the inlet density, checkpoints every 50 steps; adjoint steps per second
+next to forward steps per second on the same lattice.
+
 ``--workload batched_sweep_64`` instead times the batched sweep: 64
 independent sphere packs (edges 48..112, radius 4..8, porosity 0.35..0.45,
 viscosity ratio in {1, 5, 10, 50}, contact angle in {30, 60, 90, 120} deg)
@@ -63,6 +69,7 @@ def workload_setup():
 
 
 BATCH_WORKLOAD = "batched_sweep_64"
+ADJOINT_WORKLOAD = "adjoint_pack_96"
 
 
 def _pc_inlet(G=3.5, minor=0.03, pc=0.02):
@@ -404,6 +411,73 @@ def run_batch(args, rank, world):
         print(json.dumps(line), flush=True)
 
 
+def run_adjoint(args, rank, world):
+    import torch
+
+    from paper_2207_01534_gb300 import inputs
+
+    solid, r1, r2 = inputs.adjoint_pack_96()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    from paper_2207_01534_gb300 import lbm
+
+    lbm.load()
+    nsteps, every = 500, 50
+    nf = int((solid == 0).sum())
+    kw = dict(tau=inputs.tau_for_viscosity_ratio(10.0), G=3.5, xi=inputs.xi_of_theta(45.0), periodic=(1, 1, 0),
+              open_axis=2, rho_in1=_pc_inlet(pc=0.0), rho_out2=1.0, sample=(8, 88))
+    stream = torch.cuda.Stream()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    with torch.cuda.stream(stream):
+        lat = lbm.Lattice(solid, storage="fp32", kernel="split", stream=stream.cuda_stream, **kw)
+        gx = torch.zeros(solid.shape, dtype=torch.float32, device="cuda")
+        # warm-up: one short record + reverse pass
+        lat.init_densities(r1, r2)
+        lat.record(2 * every, every)
+        lat.adjoint(1.0, gx)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        lat.init_densities(r1, r2)
+        l0 = lat.info()["launches"]
+        ev[0].record(stream)
+        lat.step(nsteps)
+        ev[1].record(stream)
+        lat.init_densities(r1, r2)
+        ev[2].record(stream)
+        lat.record(nsteps, every)
+        ev[3].record(stream)
+        J, grin = lat.adjoint(1.0, gx)
+        ev[4].record(stream)
+        torch.cuda.synchronize()
+        clk = clocks.stop()
+        launches = lat.info()["launches"] - l0
+        t_fwd = ev[0].elapsed_time(ev[1]) / 1e3
+        t_rec = ev[2].elapsed_time(ev[3]) / 1e3
+        t_adj = ev[3].elapsed_time(ev[4]) / 1e3
+        gmax = float(gx.abs().max())
+        mem = lat.info()["device_bytes"]
+    fwd_rate = nsteps / t_fwd
+    adj_rate = nsteps / (t_rec + t_adj)
+    value = nf * nsteps / (t_rec + t_adj) / 1e6
+    peak, peak_kind = peaks()
+    cfg = {"workload": ADJOINT_WORKLOAD, "grid": [96, 96, 96], "sphere_radius": 6, "porosity": 0.40, "reservoir": 8,
+           "steps": nsteps, "checkpoint_every": every, "n_fluid": nf, "M": 10, "theta_deg": 45, "Pc": 0.0,
+           "loss": "smooth S_nw of the sample slab", "storage": "fp32", "parallelism": "single",
+           "forward_steps_per_s": fwd_rate, "adjoint_steps_per_s": adj_rate,
+           "adjoint_over_forward_time": (t_rec + t_adj) / t_fwd, "record_s": t_rec, "reverse_s": t_adj,
+           "device_bytes": mem, "J": J, "dJ_drho_in1": grin, "max_abs_dJ_dxi": gmax,
+           "l2": "inputs larger than L2 (checkpoints and segment states exceed 1 GB)"}
+    line = {"metric": "adjoint MLUPS (forward record + reverse, 2-component D3Q19)", "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": nsteps, "warmup": 1, "ms_per_step": (t_rec + t_adj) * 1e3 / nsteps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": cfg, "gpu_launches": int(launches), "clocks": clk,
+            "roofline": {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
+                         "traffic": None, "peak_kind": peak_kind}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -414,7 +488,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp64", "fp16dev", "bf16dev"))
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default=WORKLOAD, choices=(WORKLOAD, BATCH_WORKLOAD))
+    ap.add_argument("--workload", default=WORKLOAD, choices=(WORKLOAD, BATCH_WORKLOAD, ADJOINT_WORKLOAD))
     ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache (batched workload)")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps > 0
@@ -424,6 +498,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == BATCH_WORKLOAD:
         run_batch(args, rank, world)
+    elif args.workload == ADJOINT_WORKLOAD:
+        run_adjoint(args, rank, world)
     else:
         run_ours(args, rank, world)
 

@@ -75,12 +75,20 @@ __global__ void k_adj_seed(DevState s, AdjState a, double inv_count)
 
 // Adjoint of the extrapolation at one plane.  sn is the state after the step
 // (its interior node holds the values the extrapolation read), PN its parity.
+// plane = 0 or 1 adjoins that plane; plane = 2 adjoins both in one launch
+// (only when nz > 3: then the two planes and their interior nodes are four
+// distinct layers and the two orders give the same result).
 template <typename TS, int PN>
-__global__ void __launch_bounds__(128) k_adj_plane(DevState sn, AdjState a, int plane)
+__global__ void __launch_bounds__(64) k_adj_plane(DevState sn, AdjState a, int planes)
 {
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    int p = blockIdx.x * blockDim.x + threadIdx.x;
+    int plane = planes;
+    if (planes == 2) {
+        plane = p >= sn.nxy ? 0 : 1;
+        if (plane == 0) p -= sn.nxy;
+    }
     if (p >= sn.nxy) return;
     const uint32_t pvb = plane == 0 ? (uint32_t)p : (uint32_t)(p + (sn.nz - 1) * sn.sxy);
     const int nb = sn.cidx[pvb];
@@ -108,16 +116,24 @@ __global__ void __launch_bounds__(128) k_adj_plane(DevState sn, AdjState a, int 
     C2 *L = reinterpret_cast<C2 *>(a.lam_in);
     C2 *Rb = reinterpret_cast<C2 *>(a.rb_in);
     const long long np = sn.npad;
+    // everything is read first, then written (the plane node and its interior
+    // node are distinct cells; keeping the values in registers lets all loads
+    // be in flight at once)
+    C2 lb[19], li[19];
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        lb[i] = L[i * np + nb];
+        li[i] = L[i * np + ni];
+    }
     // fold the plane node's density part into its populations
     const C2 rbb = Rb[pvb];
-    Rb[pvb] = mk2(C(0), C(0));
     C gb = 0, rbar = 0, ub[3] = {0, 0, 0};
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        C2 l = add2(L[i * np + nb], rbb);
+        C2 l = add2(lb[i], rbb);
         const C mu = plane == 0 ? l.x : l.y;
         if (plane == 0) l.x = C(0); else l.y = C(0);
-        L[i * np + nb] = l;
+        lb[i] = l;
         const C eu = ex(i) * u[0] + ey(i) * u[1] + ez(i) * u[2];
         const C feq1 = wgt<C>(i) * (C(1) + C(3) * eu + C(4.5) * eu * eu - C(1.5) * usq);
         gb += mu * feq1;
@@ -127,19 +143,18 @@ __global__ void __launch_bounds__(128) k_adj_plane(DevState sn, AdjState a, int 
         ub[1] += k * (C(3) * ey(i) + C(9) * eu * ey(i) - C(3) * u[1]);
         ub[2] += k * (C(3) * ez(i) + C(9) * eu * ez(i) - C(3) * u[2]);
         // the f(xI) term
-        C2 li = L[i * np + ni];
-        if (plane == 0) li.x += mu; else li.y += mu;
-        L[i * np + ni] = li;
+        if (plane == 0) li[i].x += mu; else li[i].y += mu;
     }
     const C ubu = ub[0] * u[0] + ub[1] * u[1] + ub[2] * u[2];
 #pragma unroll
     for (int j = 0; j < 19; ++j) {
         const C du = (ex(j) * ub[0] + ey(j) * ub[1] + ez(j) * ub[2] - ubu) / R;
-        C2 li = L[j * np + ni];
-        li = add2(li, mk2(du, du));
-        if (plane == 0) li.x += rbar; else li.y += rbar;
-        L[j * np + ni] = li;
+        C2 v = add2(li[j], mk2(du, du));
+        if (plane == 0) v.x += rbar; else v.y += rbar;
+        L[j * np + ni] = v;
+        L[j * np + nb] = lb[j];
     }
+    Rb[pvb] = mk2(C(0), C(0));
     if (plane == 0) a.grin[p] += (double)gb;
 }
 
@@ -174,14 +189,33 @@ __device__ __forceinline__ C2 gather_abar(const C2 *ab, long long nv, uint32_t p
 }
 
 // Streaming, collision and local moments in reverse at node n; P is the parity
-// of the step's state st (psi holds its densities and wall densities).
+// of the step's state st (psi holds its densities and wall densities).  The
+// forward populations are only needed through the momenta and the sum
+// sum_i L_i . f_i of the tau derivative, so they are folded as they load and
+// the kernel keeps just the 19 adjoint pairs live (two blocks per SM).
+// The 19 adjoint pairs of a thread live in shared memory ([19][blockDim]
+// pairs, dynamic) rather than registers, which leaves room for three blocks
+// of 256 threads per SM in FP32.
+template <typename TS>
+struct AdjOcc {  // resident blocks per SM the register budget is sized for
+    static constexpr int blocks = 3;
+};
+template <>
+struct AdjOcc<double> {
+    static constexpr int blocks = 1;
+};
+
 template <typename TS, int P>
-__global__ void __launch_bounds__(256) k_adj_node(DevState st, AdjState a)
+__global__ void __launch_bounds__(256, AdjOcc<TS>::blocks) k_adj_node(DevState st, AdjState a)
 {
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
+    using S2 = typename Traits<TS>::S2;
+    extern __shared__ __align__(16) unsigned char adj_smem[];
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
     if (n >= st.n_fluid) return;
+    C2 *ls = reinterpret_cast<C2 *>(adj_smem) + threadIdx.x;  // ls[i * blockDim.x]
+    const int ld = blockDim.x;
     const uint32_t pv = st.pvox[n];
     const uint32_t fl = st.nflags[n];
     const Nbr b = make_nbr(fl, st);
@@ -189,24 +223,40 @@ __global__ void __launch_bounds__(256) k_adj_node(DevState st, AdjState a)
     const C2 *Lin = reinterpret_cast<const C2 *>(a.lam_in);
     const C2 *Rin = reinterpret_cast<const C2 *>(a.rb_in);
     // adjoint of the post-collision populations (streaming transposed)
-    C2 ls[19];
     const C2 ry = Rin[pv];
     ls[0] = add2(Lin[n], ry);
 #pragma unroll
     for (int i = 1; i < 19; ++i) {
         if (ez(i) != 0 && outside(i, fl)) {
-            ls[i] = mk2(C(0), C(0));
+            ls[i * ld] = mk2(C(0), C(0));
             continue;
         }
         const int off = nb_off(i, b);
         const int c = __ldg(st.cidx + ((int)pv + off));
-        ls[i] = c >= 0 ? add2(Lin[i * np + c], Rin[(int)pv + off]) : add2(Lin[opp(i) * np + n], ry);
+        ls[i * ld] = c >= 0 ? add2(Lin[i * np + c], Rin[(int)pv + off]) : add2(Lin[opp(i) * np + n], ry);
     }
-    // the forward quantities of the node
-    C2 f[19], dm;
-    load_pops<TS, P>(f, dm, n, pv, fl, b, st);
-    const C2 rho = density_of<TS>(dm, st);
+    // the forward quantities of the node: rho from the density pass, the
+    // momenta and L.f from the populations
     const C2 *psi = reinterpret_cast<const C2 *>(st.psi) + pv;
+    const C2 rho = psi[0];
+    C2 m[3] = {mk2(C(0), C(0)), mk2(C(0), C(0)), mk2(C(0), C(0))};
+    C2 lf = mul2(ls[0], ld_rest<TS, false>(st, n));
+    {
+        const S2 *M = reinterpret_cast<const S2 *>(st.f);
+        const S2 *B = reinterpret_cast<const S2 *>(st.bc);
+        const bool plane = P == 1 && (fl & (F_INLET | F_OUTLET));
+#pragma unroll
+        for (int j = 1; j < 19; ++j) {
+            const S2 *q = (ez(j) != 0 && plane && outside(j, fl)) ? B + bc_cell(j, pv, fl, st)
+                                                                   : M + slot_in_block<P>(j, n, pv, b, st);
+            const C2 fi = Traits<TS>::load(q, ref_of<TS>(st, opp(j)));  // f_opp(j)
+            const int i = opp(j);
+            lf = fma2(ls[i * ld], fi, lf);
+            if (ex(i)) m[0] = ex(i) > 0 ? add2(m[0], fi) : sub2(m[0], fi);
+            if (ey(i)) m[1] = ey(i) > 0 ? add2(m[1], fi) : sub2(m[1], fi);
+            if (ez(i)) m[2] = ez(i) > 0 ? add2(m[2], fi) : sub2(m[2], fi);
+        }
+    }
     C2 A[3] = {mk2(C(0), C(0)), mk2(C(0), C(0)), mk2(C(0), C(0))};  // (.x: psi1 sums, .y: psi2 sums)
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
@@ -223,13 +273,6 @@ __global__ void __launch_bounds__(256) k_adj_node(DevState st, AdjState a)
     C2 F[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) F[k] = mk2(rho.x * (-G * A[k].y + g[k]), rho.y * (-G * A[k].x + g[k]));
-    C2 m[3] = {mk2(C(0), C(0)), mk2(C(0), C(0)), mk2(C(0), C(0))};
-#pragma unroll
-    for (int i = 1; i < 19; ++i) {
-        if (ex(i)) m[0] = ex(i) > 0 ? add2(m[0], f[i]) : sub2(m[0], f[i]);
-        if (ey(i)) m[1] = ey(i) > 0 ? add2(m[1], f[i]) : sub2(m[1], f[i]);
-        if (ez(i)) m[2] = ez(i) > 0 ? add2(m[2], f[i]) : sub2(m[2], f[i]);
-    }
     const C R = rho.x + rho.y;
     const C h = st.velocity_shift ? C(0.5) : C(0);
     C u[3];
@@ -239,14 +282,14 @@ __global__ void __launch_bounds__(256) k_adj_node(DevState st, AdjState a)
     const C om = C(1) / tau;
     const C cf = C(1) - C(0.5) * om;
     const C usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
-    // collision transposed
+    // collision transposed; d f*/d tau = ((f - feq) + S / 2) / tau^2
     C2 rb = mk2(C(0), C(0));
     C ub[3] = {0, 0, 0};
     C2 Fb[3] = {mk2(C(0), C(0)), mk2(C(0), C(0)), mk2(C(0), C(0))};
-    C taub = 0;
+    C taub = lf.x + lf.y;
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        const C2 L = ls[i];
+        const C2 L = ls[i * ld];
         const C w = wgt<C>(i);
         const C eu = ex(i) * u[0] + ey(i) * u[1] + ez(i) * u[2];
         const C feq1 = w * (C(1) + C(3) * eu + C(4.5) * eu * eu - C(1.5) * usq);
@@ -256,9 +299,7 @@ __global__ void __launch_bounds__(256) k_adj_node(DevState st, AdjState a)
         const C2 S = mk2(w * (C(3) * (eF.x - uF.x) + C(9) * eu * eF.x), w * (C(3) * (eF.y - uF.y) + C(9) * eu * eF.y));
         rb = fma2(bc2<C2>(feq1 * om), L, rb);
         const C Lr = L.x * rho.x + L.y * rho.y;  // sum_s L^s rho^s
-        const C2 LeF = mk2(L.x * eF.x, L.y * eF.y);
-        const C LeFs = LeF.x + LeF.y;
-        const C Ls = L.x + L.y;
+        const C LeFs = L.x * eF.x + L.y * eF.y;
         ub[0] += w * (om * Lr * (C(3) * ex(i) + C(9) * eu * ex(i) - C(3) * u[0]) +
                       cf * (C(-3) * (L.x * F[0].x + L.y * F[0].y) + C(9) * ex(i) * LeFs));
         ub[1] += w * (om * Lr * (C(3) * ey(i) + C(9) * eu * ey(i) - C(3) * u[1]) +
@@ -271,9 +312,7 @@ __global__ void __launch_bounds__(256) k_adj_node(DevState st, AdjState a)
         Fb[0] = fma2(bc2<C2>(k0), L, Fb[0]);
         Fb[1] = fma2(bc2<C2>(k1), L, Fb[1]);
         Fb[2] = fma2(bc2<C2>(k2), L, Fb[2]);
-        // d f* / d tau = ((f - feq) + S / 2) / tau^2
-        taub += L.x * (f[i].x - rho.x * feq1 + C(0.5) * S.x) + L.y * (f[i].y - rho.y * feq1 + C(0.5) * S.y);
-        (void)Ls;
+        taub += -Lr * feq1 + C(0.5) * (L.x * S.x + L.y * S.y);
     }
     taub *= om * om;
     // tau = (rho1 tau1 + rho2 tau2) / R
@@ -301,7 +340,7 @@ __global__ void __launch_bounds__(256) k_adj_node(DevState st, AdjState a)
     const C2 keep = bc2<C2>(C(1) - om);
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
-        C2 v = fma2(keep, ls[i], rb);
+        C2 v = fma2(keep, ls[i * ld], rb);
         if (ex(i)) v = ex(i) > 0 ? add2(v, mb[0]) : sub2(v, mb[0]);
         if (ey(i)) v = ey(i) > 0 ? add2(v, mb[1]) : sub2(v, mb[1]);
         if (ez(i)) v = ez(i) > 0 ? add2(v, mb[2]) : sub2(v, mb[2]);
@@ -353,20 +392,49 @@ __global__ void __launch_bounds__(256) k_adj_dens(DevState st, AdjState a)
     const int z = (int)(pv / (uint32_t)st.sxy);
     const C2 *ab = reinterpret_cast<const C2 *>(a.abar);
     const C2 *wb = reinterpret_cast<const C2 *>(a.wbar);
-    // y - e_j: in the domain unless it crosses an open plane
+    // y - e_j: in the domain unless it crosses an open plane.  abar is zero
+    // on solid voxels and wbar on fluid ones (both are cleared before the
+    // pass and only written on their own voxels), so neither gather needs to
+    // look the neighbour's kind up.
     auto in_dom = [&](int j) { return !(ez(j) != 0 && outside(opp(j), fl)); };
-    const C2 gsum = gather_abar<C, C2>(
-        ab, st.nv, pv, z, st.nz, st.open_z,
-        [&](int j) { return in_dom(j) && __ldg(st.cidx + ((int)pv + nb_off(opp(j), b))) >= 0; },
-        [&](int j) { return nb_off(opp(j), b); });
+    const C2 gsum = gather_abar<C, C2>(ab, st.nv, pv, z, st.nz, st.open_z, in_dom,
+                                       [&](int j) { return nb_off(opp(j), b); });
     C2 r = swap2(gsum);
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
         if (!in_dom(j)) continue;
-        const int off = nb_off(opp(j), b);
-        if (__ldg(st.cidx + ((int)pv + off)) < 0) r = fma2(bc2<C2>(wgt<C>(j)), wb[(int)pv + off], r);
+        r = fma2(bc2<C2>(wgt<C>(j)), wb[(int)pv + nb_off(opp(j), b)], r);
     }
     reinterpret_cast<C2 *>(a.rb_out)[pv] = r;
+}
+
+// Out-of-place forward step for the recompute: reads the state of st and
+// writes the next one into f_out / rest_out.  Every population cell is
+// written exactly once per step (the A-A slots of a parity are a bijection
+// onto the cells), so the new buffers are complete but for the open-plane
+// boundary cells, which the extrapolation of the next density pass writes.
+template <typename TS, int P>
+__global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused_to(DevState st, void *f_out, void *rest_out)
+{
+    using C = typename Traits<TS>::C;
+    using C2 = typename Traits<TS>::C2;
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= st.n_fluid) return;
+    const uint32_t pv = st.pvox[n];
+    const uint32_t fl = st.nflags[n];
+    const Nbr b = make_nbr(fl, st);
+    C2 f[19], dm;
+    load_pops<TS, P>(f, dm, n, pv, fl, b, st);
+    const C2 rho = density_of<TS>(dm, st);
+    C2 F[3];
+    C u[3], inv_rho;
+    forces<TS>(rho, pv, fl, b, st, F);
+    mix_velocity<C, C2>(f, rho, F, st, inv_rho, u);
+    collide<C, C2>(f, rho, inv_rho, u, F, st);
+    DevState so = st;
+    so.f = f_out;
+    so.rest = rest_out;
+    store_pops<TS, P>(f, dm, n, pv, fl, b, so);
 }
 
 // dJ/dxi on the dense grid (zero off the walls), scaled by the incoming gradient
@@ -381,12 +449,23 @@ __global__ void k_adj_xi_out(DevState st, AdjState a, double scale, float *grad)
 template <typename TS>
 struct Adj {
     static void seed(const DevState &s, const AdjState &a, double inv_count, cudaStream_t st);
+    // plane 0 (inlet), 1 (outlet) or 2 (both in one launch; needs nz > 3)
     static void plane(const DevState &sn, const AdjState &a, int parity_next, int plane, cudaStream_t st);
     static void node(const DevState &s, const AdjState &a, int parity, cudaStream_t st);
     static void wall(const DevState &s, const AdjState &a, cudaStream_t st);
     static void dens(const DevState &s, const AdjState &a, cudaStream_t st);
     static void xi_out(const DevState &s, const AdjState &a, double scale, float *grad, cudaStream_t st);
+    static void fused_to(const DevState &s, int parity, void *f_out, void *rest_out, cudaStream_t st);
 };
+
+template <typename TS>
+void Adj<TS>::fused_to(const DevState &s, int parity, void *f_out, void *rest_out, cudaStream_t st)
+{
+    if (s.n_fluid == 0) return;
+    const int g = (s.n_fluid + 255) / 256;
+    if (parity) k_fused_to<TS, 1><<<g, 256, 0, st>>>(s, f_out, rest_out);
+    else k_fused_to<TS, 0><<<g, 256, 0, st>>>(s, f_out, rest_out);
+}
 
 template <typename TS>
 void Adj<TS>::seed(const DevState &s, const AdjState &a, double inv_count, cudaStream_t st)
@@ -397,17 +476,25 @@ template <typename TS>
 void Adj<TS>::plane(const DevState &sn, const AdjState &a, int parity_next, int plane, cudaStream_t st)
 {
     if (!sn.open_z || sn.nxy == 0) return;
-    const int g = (sn.nxy + 127) / 128;
-    if (parity_next) k_adj_plane<TS, 1><<<g, 128, 0, st>>>(sn, a, plane);
-    else k_adj_plane<TS, 0><<<g, 128, 0, st>>>(sn, a, plane);
+    const int g = ((plane == 2 ? 2 : 1) * sn.nxy + 63) / 64;
+    if (parity_next) k_adj_plane<TS, 1><<<g, 64, 0, st>>>(sn, a, plane);
+    else k_adj_plane<TS, 0><<<g, 64, 0, st>>>(sn, a, plane);
 }
 template <typename TS>
 void Adj<TS>::node(const DevState &s, const AdjState &a, int parity, cudaStream_t st)
 {
     if (s.n_fluid == 0) return;
+    using C2 = typename Traits<TS>::C2;
+    const size_t smem = (size_t)19 * 256 * sizeof(C2);
+    static bool attr = false;  // above the 48 KB default for FP64
+    if (!attr) {
+        cudaFuncSetAttribute(k_adj_node<TS, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_adj_node<TS, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        attr = true;
+    }
     const int g = (s.n_fluid + 255) / 256;
-    if (parity) k_adj_node<TS, 1><<<g, 256, 0, st>>>(s, a);
-    else k_adj_node<TS, 0><<<g, 256, 0, st>>>(s, a);
+    if (parity) k_adj_node<TS, 1><<<g, 256, smem, st>>>(s, a);
+    else k_adj_node<TS, 0><<<g, 256, smem, st>>>(s, a);
 }
 template <typename TS>
 void Adj<TS>::wall(const DevState &s, const AdjState &a, cudaStream_t st)

@@ -85,6 +85,7 @@ struct lbm_ctx {
         std::vector<void *> ckpt;  // state at step0 + k*every
         void *final_state = nullptr;
         std::vector<void *> seg;   // states inside one segment
+        std::vector<void *> psis;  // densities (psi) of each state of a segment
         void *lam[2] = {nullptr, nullptr}, *rb[2] = {nullptr, nullptr};
         void *abar = nullptr, *wbar = nullptr, *psi = nullptr;
         double *gxi = nullptr, *grin = nullptr;
@@ -650,15 +651,6 @@ void snap_save(lbm_ctx *c, void *buf)
         cudaMemcpyAsync(b + c->f_bytes + c->rest_bytes, c->s.bc, c->bc_bytes, cudaMemcpyDeviceToDevice, c->stream);
 }
 
-void snap_load(lbm_ctx *c, const void *buf)
-{
-    const char *b = (const char *)buf;
-    cudaMemcpyAsync(c->s.f, b, c->f_bytes, cudaMemcpyDeviceToDevice, c->stream);
-    cudaMemcpyAsync(c->s.rest, b + c->f_bytes, c->rest_bytes, cudaMemcpyDeviceToDevice, c->stream);
-    if (c->bc_bytes)
-        cudaMemcpyAsync(c->s.bc, b + c->f_bytes + c->rest_bytes, c->bc_bytes, cudaMemcpyDeviceToDevice, c->stream);
-}
-
 // The lattice with its populations read from a saved state and psi in psi_buf.
 DevState snap_state(const lbm_ctx *c, void *buf, void *psi_buf)
 {
@@ -676,8 +668,10 @@ void free_record(lbm_ctx *c)
     auto &r = c->rec;
     for (void *q : r.ckpt) dfree(c, q);
     for (void *q : r.seg) dfree(c, q);
+    for (void *q : r.psis) dfree(c, q);
     r.ckpt.clear();
     r.seg.clear();
+    r.psis.clear();
     for (void **q : {&r.final_state, &r.lam[0], &r.lam[1], &r.rb[0], &r.rb[1], &r.abar, &r.wbar, &r.psi})
         if (*q) {
             dfree(c, *q);
@@ -1502,6 +1496,11 @@ lbm_status lbm_adjoint(lbm_ctx *c, double dloss, float *grad_xi, double *grad_rh
         if (!q) return fail(c, LBM_ERR_ALLOC, "lbm_adjoint: segment states");
         r.seg.push_back(q);
     }
+    while ((int64_t)r.psis.size() < r.every) {
+        void *q = dalloc(c, (size_t)c->nv * (c->storage == LBM_STORE_FP64 ? 16 : 8));
+        if (!q) return fail(c, LBM_ERR_ALLOC, "lbm_adjoint: segment densities");
+        r.psis.push_back(q);
+    }
     auto need = [&](void *&q, size_t bytes) {
         if (!q) q = dalloc(c, bytes);
         return q != nullptr;
@@ -1549,40 +1548,51 @@ lbm_status lbm_adjoint(lbm_ctx *c, double dloss, float *grad_xi, double *grad_rh
     for (int64_t k = nck - 1; k >= 0; --k) {
         const int64_t t0 = k * r.every;
         const int64_t len = std::min<int64_t>(r.every, r.n - t0);
-        // recompute the segment from its checkpoint
-        snap_load(c, r.ckpt[(size_t)k]);
-        c->step = r.step0 + t0;
+        // Recompute the segment from its checkpoint, out of place: the
+        // density pass of state q (in its own buffer) applies the pending
+        // open-plane extrapolation and writes the densities of state q into
+        // psis[q]; the collide-stream pass reads state q and writes state q + 1
+        // into the next buffer.  The live state is not touched.
         std::vector<void *> S((size_t)len + 1);
         S[0] = r.ckpt[(size_t)k];
+        for (int64_t q = 1; q < len; ++q) S[(size_t)q] = r.seg[(size_t)q - 1];
         S[(size_t)len] = k + 1 < nck ? r.ckpt[(size_t)k + 1] : r.final_state;
-        for (int64_t q = 1; q < len; ++q) {
-            enqueue_step(c, nullptr);
-            S[(size_t)q] = r.seg[(size_t)q - 1];
-            snap_save(c, S[(size_t)q]);
+        for (int64_t q = 0; q < len; ++q) {
+            const int64_t step = r.step0 + t0 + q;
+            const int par = (int)(step & 1);
+            const DevState s_q = snap_state(c, S[(size_t)q], r.psis[(size_t)q]);
+            const DevState s_n = snap_state(c, S[(size_t)q + 1], r.psis[(size_t)q]);
+            dispatch_adj(c, [&](auto tag) {
+                using TS = decltype(tag);
+                Ops<TS>::dens(s_q, par, step > 0, st, c->block);
+                Ops<TS>::wall(s_q, st, c->block);
+                if (q + 1 < len) Adj<TS>::fused_to(s_q, par, s_n.f, s_n.rest, st);
+            });
+            c->launches += q + 1 < len ? 3 : 2;
         }
         // reverse the segment's steps
         for (int64_t q = len - 1; q >= 0; --q) {
             const int par = (int)((r.step0 + t0 + q) & 1);
-            const DevState s_t = snap_state(c, S[(size_t)q], r.psi);
-            const DevState s_n = snap_state(c, S[(size_t)q + 1], r.psi);
+            const DevState s_t = snap_state(c, S[(size_t)q], r.psis[(size_t)q]);
+            const DevState s_n = snap_state(c, S[(size_t)q + 1], r.psis[(size_t)q]);
             dispatch_adj(c, [&](auto tag) {
                 using TS = decltype(tag);
-                Ops<TS>::dens(s_t, par, 0, st);
-                Ops<TS>::wall(s_t, st);
-                Adj<TS>::plane(s_n, a, 1 - par, 1, st);  // outlet (extrapolated last)
-                Adj<TS>::plane(s_n, a, 1 - par, 0, st);  // inlet
+                if (c->nz > 3) {
+                    Adj<TS>::plane(s_n, a, 1 - par, 2, st);
+                } else {
+                    Adj<TS>::plane(s_n, a, 1 - par, 1, st);  // outlet (extrapolated last)
+                    Adj<TS>::plane(s_n, a, 1 - par, 0, st);  // inlet
+                }
                 Adj<TS>::node(s_t, a, par, st);
                 Adj<TS>::wall(s_t, a, st);
                 Adj<TS>::dens(s_t, a, st);
             });
-            c->launches += 7;
+            c->launches += 5;
             std::swap(a.lam_in, a.lam_out);
             std::swap(a.rb_in, a.rb_out);
         }
     }
-    // back to the recorded final state
-    snap_load(c, r.final_state);
-    c->step = r.step_end;
+    // the recompute never touched the live state: it is still the final one
     lbm_status stt = check_launch(c, "lbm_adjoint");
     if (stt != LBM_OK) return stt;
     if (grad_xi) {

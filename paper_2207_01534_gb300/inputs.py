@@ -241,6 +241,19 @@ def drainage_init(solid, inlet_slices, rho_major=1.0, rho_minor=0.03):
     return rho1 * fluid, rho2 * fluid
 
 
+def imbibition_init(solid, outlet_slices, rho_major=1.0, rho_minor=0.03):
+    """Component 1 (non-wetting oil) everywhere, component 2 (water) in the
+    last ``outlet_slices`` z slices: the start of an imbibition, water entering
+    the oil-filled sample from the outlet side."""
+    nz = solid.shape[0]
+    rho1 = np.full(solid.shape, rho_major)
+    rho2 = np.full(solid.shape, rho_minor)
+    rho1[nz - outlet_slices:] = rho_minor
+    rho2[nz - outlet_slices:] = rho_major
+    fluid = solid == 0
+    return rho1 * fluid, rho2 * fluid
+
+
 def porosity(solid: np.ndarray, reservoir: int = 0) -> float:
     s = solid[reservoir: solid.shape[0] - reservoir] if reservoir else solid
     return float((s == 0).mean())
@@ -284,6 +297,14 @@ def batched_sample(spec):
     """(solid, rho1, rho2) of one sample of ``batched_sweep``."""
     solid = sphere_pack(spec["n"], spec["radius"], spec["porosity"], spec["seed"], reservoir=spec["reservoir"])
     r1, r2 = drainage_init(solid, spec["reservoir"])
+    return solid, r1, r2
+
+
+def adjoint_pack_96(seed_offset=2):
+    """96^3 sphere pack, radius 6, porosity 0.40, 8-slice reservoirs, with the
+    imbibition start (oil everywhere, water in the outlet reservoir)."""
+    solid = sphere_pack(96, 6.0, 0.40, SEED_BASE + seed_offset, reservoir=8)
+    r1, r2 = imbibition_init(solid, 8)
     return solid, r1, r2
 
 

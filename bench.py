@@ -59,8 +59,7 @@ def workload_setup():
     # inlet density of component 1 for a capillary pressure Pc = P_in - P_out of
     # 0.02 with the Eq. 12 pressure (inlet: rho2 ~ 0.03; outlet: rho2 = 1, rho1 ~ 0.03)
     G, minor, pc = 3.5, 0.03, 0.02
-    p_out = (1.0 + minor) / 3.0 + G / 3.0 * minor
-    rho_in1 = (p_out + pc - minor / 3.0) / (1.0 / 3.0 + G / 3.0 * minor)
+    rho_in1 = _pc_inlet(G, minor, pc)
     kw = dict(tau=tau, G=G, xi=xi, periodic=(1, 1, 0), open_axis=2, rho_in1=rho_in1, rho_out2=1.0)
     cfg = {"workload": WORKLOAD, "grid": [128, 128, 128], "sphere_radius": 8, "porosity": 0.38, "reservoir": 8,
            "M": 10, "theta_deg": 45, "G": G, "Pc": pc, "n_fluid": int((solid == 0).sum()),
@@ -73,8 +72,9 @@ ADJOINT_WORKLOAD = "adjoint_pack_96"
 
 
 def _pc_inlet(G=3.5, minor=0.03, pc=0.02):
-    p_out = (1.0 + minor) / 3.0 + G / 3.0 * minor
-    return (p_out + pc - minor / 3.0) / (1.0 / 3.0 + G / 3.0 * minor)
+    from paper_2207_01534_gb300 import drivers
+
+    return drivers.inlet_density(pc, G, minor, 1.0)
 
 
 def batch_setup(count=64):

@@ -60,7 +60,11 @@ enum {
     LBM_KERNEL_FUSED = 2  /* single persistent pass per step (see lbm_step) */
 };
 
-enum { LBM_BC_NEEM = 0 };
+/* Open-plane rule for the prescribed component (Section 2, boundary rule 1):
+ * non-equilibrium extrapolation from the first interior node, or the Zou-He
+ * method (entering populations from the node's own density, zero tangential
+ * velocity and normal non-equilibrium bounce-back). */
+enum { LBM_BC_NEEM = 0, LBM_BC_ZOU_HE = 1 };
 
 /* Field selection bits for lbm_read_fields. */
 enum {
@@ -94,7 +98,7 @@ typedef struct {
  * (Eq. 7, read as nu = c_s^2 (tau - 1/2)).  G: cohesion strength G_coh (Eq.
  * 11; the paper uses 3.5).  xi: wettability, chi^(1) = 1 + xi, chi^(2) = 1 - xi
  * (Eq. 15).  rho_in1 / rho_out2: prescribed component densities at the inlet
- * and outlet planes (non-equilibrium extrapolation).  body_force: acceleration
+ * and outlet planes.  bc: LBM_BC_* (the rule that imposes them).  body_force: acceleration
  * g, F^b = rho^sigma g (Eq. 10).  velocity_shift: 1 adds F^sigma/2 to the
  * component momenta in Eq. 8 (the explicit-forcing reading, default); 0 uses
  * the printed Eq. 4 momenta.  storage: LBM_STORE_*.  rho_ref: per-component
@@ -242,8 +246,8 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t *block_out
  * wettability xi (chi^(1,2) = 1 +/- xi in the virtual wall density, Eq. 15)
  * and the inlet density rho_in1 of the open-boundary extrapolation (Section
  * 2).  The paper has no adjoint; this is the exact discrete adjoint of the
- * step as implemented (FP32 or FP64 storage, split schedule, single lattice;
- * LBM_ERR_UNSUPPORTED otherwise).
+ * step as implemented (FP32 or FP64 storage, split schedule, single lattice,
+ * LBM_BC_NEEM open planes; LBM_ERR_UNSUPPORTED otherwise).
  *
  * lbm_set_xi_field sets xi on every wall voxel from a dense nx*ny*nz float
  * array (host pointer when on_device = 0, device pointer otherwise); values

@@ -41,6 +41,7 @@ def _load():
     lib.ora_step_count.restype = ctypes.c_long
     lib.ora_fields.argtypes = [ctypes.c_void_p] + [dp] * 6
     lib.ora_saturation.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, dp]
+    lib.ora_set_bc.argtypes = [ctypes.c_void_p, ctypes.c_int]
     lib.ora_record.argtypes = [ctypes.c_void_p, ctypes.c_long]
     lib.ora_adjoint.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, dp]
     lib.ora_lattice.argtypes = [ip, dp, ip]
@@ -110,7 +111,7 @@ class Oracle:
     """
 
     def __init__(self, solid, tau=(1.0, 1.0), G=3.5, xi=0.0, xi_field=None, periodic=(1, 1, 1),
-                 open_axis=-1, rho_in1=1.0, rho_out2=1.0, body_force=(0.0, 0.0, 0.0), velocity_shift=1):
+                 open_axis=-1, rho_in1=1.0, rho_out2=1.0, body_force=(0.0, 0.0, 0.0), velocity_shift=1, bc="neem"):
         lib = _load()
         self._lib = lib
         solid = np.ascontiguousarray(solid, dtype=np.uint8)
@@ -133,6 +134,8 @@ class Oracle:
             raise ValueError(err.value.decode())
         self._h = h
         self._keep = (xf,)
+        assert bc in ("neem", "zou_he")
+        lib.ora_set_bc(h, 1 if bc == "zou_he" else 0)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -200,6 +203,8 @@ class Oracle:
         rc = self._lib.ora_adjoint(self._h, int(lo), int(hi), _dp(sd) if sd is not None else None, _dp(gxi),
                                    _dp(grin), _dp(gf) if gf is not None else None,
                                    _dp(gz) if gz is not None else None)
+        if rc == -2:
+            raise NotImplementedError("the oracle adjoint covers the extrapolation boundary only")
         if rc != 0:
             raise RuntimeError("record() first")
         out = {"xi": gxi, "rho_in1": float(grin[0])}

@@ -25,8 +25,9 @@
  *   5. collision with the explicit-forcing source term        (Eqs. 1, 2, 9)
  *   6. pull streaming with half-way bounce-back, periodic wrap
  *      and frozen missing populations at the open planes      (Eq. 1, Section 2)
- *   7. non-equilibrium extrapolation of the prescribed
- *      component at the inlet (component 1) and outlet (2)    (Section 2, 4.1)
+ *   7. non-equilibrium extrapolation (or the Zou-He method) for
+ *      the prescribed component at the inlet (component 1) and
+ *      outlet (2)                                              (Section 2, 4.1)
  *
  * Parity pins: every function is checked by tests against closed forms,
  * conservation laws, symmetries and the paper's printed physics (tests marked
@@ -77,6 +78,7 @@ typedef struct ora {
     double *mom[2];    /* sum_i e_i f_i, [3*v + a] */
     double *F[2];      /* total force, [3*v + a] */
     long step;
+    int bc;            /* 0: non-equilibrium extrapolation, 1: Zou-He */
     double *tape;      /* recorded states for the adjoint: (tape_len) x [2][Q*nv] */
     long tape_len;
 } ora_t;
@@ -503,6 +505,59 @@ static void neem_plane(ora_t *o, int plane, int comp, double rho_b, int inward)
     }
 }
 
+/* Step 7 with the Zou-He method (Section 2 rule 1, Zou and He 1997): at an
+ * open-plane node xb the prescribed component's populations that enter from
+ * outside are unknown after streaming.  They are set so that the node's
+ * component density is rho_b, its velocity is normal to the plane (no
+ * tangential velocity), and the non-equilibrium parts of each unknown and its
+ * opposite agree up to a tangential correction:
+ *   f_i = f_opp(i) + 6 w_i rho_b (e_i . n) u_n - (e_i,t1 N_t1 + e_i,t2 N_t2),
+ * with n the inward normal, u_n the normal velocity fixed by the density,
+ *   rho_b u_n = rho_b - (sum of the in-plane populations
+ *                        + 2 sum of the outgoing populations),
+ * and N_t = (1/2) sum over in-plane populations of e_t f (so the tangential
+ * momentum vanishes).  The other populations of the node are kept. */
+static void zou_he_plane(ora_t *o, int plane, int comp, double rho_b, int inward)
+{
+    const int ax = o->open_axis;
+    const long nv = o->nv;
+    const int a1 = (ax + 1) % 3, a2 = (ax + 2) % 3;
+#pragma omp parallel for schedule(static)
+    for (int p2 = 0; p2 < o->n[a2]; ++p2) {
+        for (int p1 = 0; p1 < o->n[a1]; ++p1) {
+            int c[3];
+            c[ax] = plane;
+            c[a1] = p1;
+            c[a2] = p2;
+            const long xb = vid(o, c);
+            if (o->solid[xb]) continue;
+            double *f = o->f[comp];
+            double s0 = 0, sout = 0, nt[3] = {0, 0, 0};
+            for (int i = 0; i < Q; ++i) {
+                const int e[3] = {EX[i], EY[i], EZ[i]};
+                const int en = e[ax] * inward; /* +1: enters the domain here */
+                const double fi = f[i * nv + xb];
+                if (en == 0) {
+                    s0 += fi;
+                    nt[a1] += e[a1] * fi;
+                    nt[a2] += e[a2] * fi;
+                } else if (en < 0) {
+                    sout += fi;
+                }
+            }
+            const double jn = rho_b - (s0 + 2.0 * sout); /* rho_b u_n */
+            for (int i = 0; i < Q; ++i) {
+                const int e[3] = {EX[i], EY[i], EZ[i]};
+                if (e[ax] * inward <= 0) continue;
+                const int o_i = o->opp[i];
+                f[i * nv + xb] = f[o_i * nv + xb] + 6.0 * WT[i] * jn - 0.5 * (e[a1] * nt[a1] + e[a2] * nt[a2]);
+            }
+        }
+    }
+}
+
+void ora_set_bc(ora_t *o, int bc) { o->bc = bc; }
+
 void ora_step(ora_t *o, long nsteps)
 {
     for (long t = 0; t < nsteps; ++t) {
@@ -511,7 +566,10 @@ void ora_step(ora_t *o, long nsteps)
         compute_forces(o);
         collide(o);
         stream(o);
-        if (o->open_axis >= 0) {
+        if (o->open_axis >= 0 && o->bc == 1) {
+            zou_he_plane(o, 0, 0, o->rho_in1, +1);
+            zou_he_plane(o, o->n[o->open_axis] - 1, 1, o->rho_out2, -1);
+        } else if (o->open_axis >= 0) {
             neem_plane(o, 0, 0, o->rho_in1, +1);
             neem_plane(o, o->n[o->open_axis] - 1, 1, o->rho_out2, -1);
         }
@@ -716,6 +774,7 @@ int ora_adjoint(ora_t *o, int lo, int hi, const double *seed, double *grad_xi, d
                 double *grad_f, double *grad_frozen)
 {
     if (!o->tape || o->tape_len < 1) return -1;
+    if (o->open_axis >= 0 && o->bc != 0) return -2; /* the reverse pass covers the extrapolation only */
     const long nv = o->nv, n = o->tape_len - 1;
     const size_t one = (size_t)Q * nv;
     double *lam[2], *lamS[2], *gfz[2], *psib[2], *rhob[2];

@@ -686,7 +686,7 @@ void free_record(lbm_ctx *c)
 bool adjoint_supported(const lbm_ctx *c)
 {
     return c->subs.empty() && !c->parent && c->kernel != LBM_KERNEL_FUSED &&
-           (c->storage == LBM_STORE_FP32 || c->storage == LBM_STORE_FP64);
+           (c->storage == LBM_STORE_FP32 || c->storage == LBM_STORE_FP64) && !(c->s.open_z && c->s.zou_he);
 }
 
 template <class Fn>
@@ -750,7 +750,7 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     if (p->storage < LBM_STORE_FP32 || p->storage > LBM_STORE_BF16DEV)
         return fail(nullptr, LBM_ERR_UNSUPPORTED, "unknown storage type");
     if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau must exceed 1/2");
-    if (p->bc != LBM_BC_NEEM) return fail(nullptr, LBM_ERR_UNSUPPORTED, "only the NEEM boundary is supported");
+    if (p->bc != LBM_BC_NEEM && p->bc != LBM_BC_ZOU_HE) return fail(nullptr, LBM_ERR_UNSUPPORTED, "unknown open-plane rule");
     if (p->reduce_every < 0) return fail(nullptr, LBM_ERR_ARG, "reduce_every must be >= 0");
 
     const int per[3] = {g->periodic[0] ? 1 : 0, g->periodic[1] ? 1 : 0, g->periodic[2] ? 1 : 0};
@@ -863,6 +863,7 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     s.nv = nv;
     s.n_wall = (int32_t)NW;
     s.open_z = open_z ? 1 : 0;
+    s.zou_he = p->bc == LBM_BC_ZOU_HE ? 1 : 0;
     s.nxy = nxy;
     s.sample_lo = g->sample_lo;
     s.sample_hi = g->sample_hi;
@@ -1443,8 +1444,8 @@ lbm_status lbm_record(lbm_ctx *c, int64_t nsteps, int32_t every)
 {
     if (!c || nsteps < 1 || every < 1) return LBM_ERR_ARG;
     if (!adjoint_supported(c))
-        return fail(c, LBM_ERR_UNSUPPORTED, "the reverse pass needs a single lattice with FP32 or FP64 storage and "
-                                            "the split schedule");
+        return fail(c, LBM_ERR_UNSUPPORTED, "the reverse pass needs a single lattice with FP32 or FP64 storage, "
+                                            "the split schedule and the extrapolation open-plane rule");
     auto &r = c->rec;
     const int64_t nck = (nsteps + every - 1) / every;
     const size_t sb = state_bytes(c);

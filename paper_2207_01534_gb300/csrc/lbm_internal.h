@@ -44,6 +44,7 @@ struct DevState {
     // initial values of the non-prescribed component's missing populations,
     // [plane][k][nxy] (double).
     int32_t open_z;
+    int32_t zou_he;          // plane rule for the prescribed component: 0 extrapolation, 1 Zou-He
     void *bc;
     const double *frozen;
     int32_t nxy;

@@ -619,12 +619,66 @@ __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused(DevState s)
 // f_i(xb) = f^eq_i(rho_b, u) + f_i(xi) - f^eq_i(rho(xi), u) with u the
 // barycentric velocity of xi; the other component's missing populations get
 // their initial values back (Section 2).
+// Zou-He form: the prescribed component's entering populations from the
+// node's own known ones, so that its density is rho_b, its tangential
+// momentum vanishes and f_i - f_opp(i) = 6 w_i rho_b u_n for the normal pair:
+// with j_n = rho_b - (in-plane sum + 2 outgoing sum) and N_t = half the
+// in-plane tangential momentum, f_i = f_opp(i) + 6 w_i j_n - e_i,t . N.
+template <typename TS, int PN, bool L2ONLY>
+__device__ __forceinline__ void zou_he_node(int plane, int nb, uint32_t pvb, uint32_t flb, const DevState &s)
+{
+    using C = typename Traits<TS>::C;
+    using C2 = typename Traits<TS>::C2;
+    using S2 = typename Traits<TS>::S2;
+    const Nbr bb = make_nbr(flb, s);
+    C2 f[19], dm;
+    load_pops<TS, PN, L2ONLY>(f, dm, nb, pvb, flb, bb, s);
+    const int pc = plane;               // prescribed component
+    const int dir = plane == 0 ? 1 : -1;  // e_z of the entering directions
+    C s0 = 0, sout = 0, nx = 0, ny = 0;
+#pragma unroll
+    for (int i = 0; i < 19; ++i) {
+        const C v = pc == 0 ? f[i].x : f[i].y;
+        if (ez(i) == 0) {
+            s0 += v;
+            nx += ex(i) * v;
+            ny += ey(i) * v;
+        } else if (ez(i) == -dir) {
+            sout += v;
+        }
+    }
+    const C rb = (C)(plane == 0 ? s.rho_in1 : s.rho_out2);
+    const C jn = rb - (s0 + C(2) * sout);
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const int i = miss_dir(plane, k);
+        const C fo = pc == 0 ? f[opp(i)].x : f[opp(i)].y;
+        const C v = fo + C(6) * wgt<C>(i) * jn - C(0.5) * (ex(i) * nx + ey(i) * ny);
+        S2 *q = slot_ptr<TS, PN>(opp(i), nb, pvb, flb, bb, s);
+        Traits<TS>::store1(q, pc, v, pc == 0 ? ref_of<TS>(s, i).x : ref_of<TS>(s, i).y);
+    }
+}
+
 template <typename TS, int PN, bool L2ONLY>
 __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb, uint32_t flb, const DevState &s)
 {
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
     using S2 = typename Traits<TS>::S2;
+    if (s.zou_he) {
+        zou_he_node<TS, PN, L2ONLY>(plane, nb, pvb, flb, s);
+        // the other component's entering populations keep their initial values
+        const Nbr bb = make_nbr(flb, s);
+        const int qc = 1 - plane;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int i = miss_dir(plane, k);
+            const C v = (C)s.frozen[(long long)(plane * 5 + k) * s.nxy + p];
+            S2 *q = slot_ptr<TS, PN>(opp(i), nb, pvb, flb, bb, s);
+            Traits<TS>::store1(q, qc, v, qc == 0 ? ref_of<TS>(s, i).x : ref_of<TS>(s, i).y);
+        }
+        return;
+    }
     const uint32_t pvi = plane == 0 ? pvb + s.sxy : pvb - s.sxy;
     const int ni = s.cidx[pvi];
     const uint32_t fli = s.nflags[ni];

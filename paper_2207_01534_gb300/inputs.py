@@ -229,6 +229,20 @@ def grf_rock(n, corr_len, porosity, seed, reservoir=8, shape=None):
     return keep_percolating(solid, True)
 
 
+def add_lateral_walls(solid: np.ndarray, axes=(0, 1)) -> np.ndarray:
+    """Close the lateral faces with solid voxels (a core holder, Section 4.2):
+    axes 0 / 1 are x / y.  Such a geometry is run with those axes
+    non-periodic."""
+    s = solid.copy()
+    if 0 in axes:
+        s[:, :, 0] = 1
+        s[:, :, -1] = 1
+    if 1 in axes:
+        s[:, 0, :] = 1
+        s[:, -1, :] = 1
+    return s
+
+
 def drainage_init(solid, inlet_slices, rho_major=1.0, rho_minor=0.03):
     """Component 2 (wetting water) everywhere, component 1 (oil) in the first
     ``inlet_slices`` z slices (Section 4.1 initial state)."""

@@ -19,6 +19,7 @@ from . import build as _build
 LBM_OK = 0
 STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_ALLOC", -3: "LBM_ERR_CUDA", -4: "LBM_ERR_NONFINITE",
           -5: "LBM_ERR_DRIFT", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_UNSUPPORTED"}
+BC = {"neem": 0, "zou_he": 1}
 STORAGE = {"fp32": 0, "fp64": 1, "fp16dev": 2, "bf16dev": 3}
 KERNEL = {"auto": 0, "split": 1, "fused": 2}
 FIELDS = ("rho1", "rho2", "ux", "uy", "uz", "P")
@@ -152,7 +153,7 @@ def saturation_static(rho1_ptr, rho2_ptr, sample_ptr, n, out_ptr, stream=0):
 
 def _geometry_params(lib, solid, tau=(1.0, 1.0), G=3.5, xi=0.0, xi_field=None, periodic=(1, 1, 1), open_axis=-1,
                      rho_in1=1.0, rho_out2=1.0, body_force=(0.0, 0.0, 0.0), velocity_shift=1, storage="fp32",
-                     kernel="auto", sample=(0, 0), reduce_every=0, drift_limit=1e-6, rho_ref=(0.0, 0.0)):
+                     kernel="auto", sample=(0, 0), reduce_every=0, drift_limit=1e-6, rho_ref=(0.0, 0.0), bc="neem"):
     """lbm_geometry and lbm_params of one lattice, plus the arrays they point
     to (keep them alive until lbm_create returns)."""
     solid = np.ascontiguousarray(solid, dtype=np.uint8)
@@ -184,6 +185,7 @@ def _geometry_params(lib, solid, tau=(1.0, 1.0), G=3.5, xi=0.0, xi_field=None, p
     p.reduce_every = int(reduce_every)
     p.drift_limit = float(drift_limit)
     p.rho_ref[0], p.rho_ref[1] = float(rho_ref[0]), float(rho_ref[1])
+    p.bc = BC[bc]
     return g, p, (solid, xf)
 
 

@@ -1,0 +1,42 @@
+"""Host logic of the experiment drivers and geometry helpers (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2207_01534_gb300 import drivers, inputs
+
+
+@pytest.mark.parametrize("pc", [0.0, 0.01, 0.035])
+def test_inlet_density_gives_the_capillary_pressure(pc):
+    rin = drivers.inlet_density(pc, G=3.5, minor=0.03, rho_out2=1.0)
+    p_in = drivers.pressure(rin, 0.03, 3.5)
+    p_out = drivers.pressure(0.03, 1.0, 3.5)
+    assert abs((p_in - p_out) - pc) < 1e-15
+
+
+@pytest.mark.parametrize("theta_water", [60.0, 90.0, 115.0])
+def test_cap_angle_of_an_exact_circle(theta_water):
+    """A sharp-interface cap cut from a circle whose angle with the wall plane
+    is known: the chord-and-height construction recovers it."""
+    nx, nz, wall = 160, 60, 0.5
+    R = 24.0
+    th1 = math.radians(180.0 - theta_water)  # angle inside the cap
+    zc = wall - R * math.cos(th1)           # centre height
+    z = np.arange(nz)[:, None]
+    x = np.arange(nx)[None, :]
+    d = np.sqrt((x - nx / 2) ** 2 + (z - zc) ** 2)
+    phi = np.where(z > wall, R - d, -1.0)       # > 0 inside the cap, linear across the interface
+    rho1 = (1 + np.tanh(phi)) / 2
+    rho2 = 1 - rho1
+    got = drivers.cap_angle(rho1[:, None, :], rho2[:, None, :], wall_z=wall, base_height=5.0)
+    assert abs(got - theta_water) < 1.5
+
+
+def test_lateral_walls():
+    s = np.zeros((5, 4, 6), np.uint8)
+    w = inputs.add_lateral_walls(s)
+    assert w[:, :, 0].all() and w[:, :, -1].all() and w[:, 0, :].all() and w[:, -1, :].all()
+    assert not w[:, 1:-1, 1:-1].any()
+    wx = inputs.add_lateral_walls(s, axes=(0,))
+    assert wx[:, :, 0].all() and not wx[:, 1:-1, 1:-1].any() and not wx[:, 0, 1:-1].any()

@@ -133,14 +133,16 @@ def _open_porous(n=(30, 16, 14), seed=11, res=4):
     return solid
 
 
+@pytest.mark.parametrize("bc", ["neem", "zou_he"])
 @pytest.mark.parametrize("storage,tol", [("fp32", TOL_FP32_RHO), ("fp64", TOL_FP64_RHO)])
-def test_open_drainage_porous(lbm, sched, storage, tol):
-    """Drainage through a porous slab with NEEM inlet/outlet, frozen missing
-    populations, mirrored pseudopotential at the planes, theta = 45 deg, M = 10."""
+def test_open_drainage_porous(lbm, sched, storage, tol, bc):
+    """Drainage through a porous slab with NEEM or Zou-He inlet/outlet, frozen
+    missing populations, mirrored pseudopotential at the planes, theta = 45
+    deg, M = 10."""
     solid = _open_porous()
     r1, r2 = inputs.drainage_init(solid, 4)
     kw = dict(tau=inputs.tau_for_viscosity_ratio(10.0), G=3.5, xi=inputs.xi_of_theta(45.0), periodic=(1, 1, 0),
-              open_axis=2, rho_in1=1.08, rho_out2=1.0)
+              open_axis=2, rho_in1=1.08, rho_out2=1.0, bc=bc)
     g, o = _pair(lbm, solid, storage, sched, **kw)
     g.init_densities(r1, r2)
     o.init_densities(r1, r2)

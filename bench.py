@@ -484,7 +484,7 @@ def main():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--kernel", default="auto", choices=("auto", "split", "fused"))
+    ap.add_argument("--kernel", default="auto", choices=("auto", "split", "fused", "wave", "push"))
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp64", "fp16dev", "bf16dev"))
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -57,7 +57,9 @@ enum {
 enum {
     LBM_KERNEL_AUTO = 0,
     LBM_KERNEL_SPLIT = 1, /* density, wall and fused collide-stream passes */
-    LBM_KERNEL_FUSED = 2  /* single persistent pass per step (see lbm_step) */
+    LBM_KERNEL_FUSED = 2, /* single persistent pass per step (see lbm_step) */
+    LBM_KERNEL_WAVE = 3,  /* the split passes per z slab, as a dependency graph (see lbm_step) */
+    LBM_KERNEL_PUSH = 4   /* collide-stream pass that also accumulates the next densities (FP32; see lbm_step) */
 };
 
 /* Open-plane rule for the prescribed component (Section 2, boundary rule 1):
@@ -226,7 +228,27 @@ lbm_status lbm_batch_get(lbm_ctx *batch, int32_t k, lbm_ctx **sample);
  * reduce_every = 0 and n >= 4 replays two steps at a time from a CUDA graph,
  * captured once on a private stream at the first even step after step 0 and
  * recaptured after any change of the lattice's parameters.  Setting the
- * environment variable LBM_NO_GRAPH disables it. */
+ * environment variable LBM_NO_GRAPH disables it.
+ *
+ * LBM_KERNEL_WAVE (single lattices): the same three passes, launched per slab
+ * of whole z planes (at least two per slab) from a graph of G steps (G = 4, or
+ * the environment variable LBM_WAVE_STEPS, even) in which each pass of a slab
+ * waits only for the passes of the slabs it reads: density(t, k) after
+ * collide-stream(t-1, k-1..k+1), wall(t, k) after density(t, k-1..k+1),
+ * collide-stream(t, k) after density and wall of (t, k-1..k+1).  Slabs of one
+ * step and consecutive steps overlap, and a slab's populations are read twice
+ * while they are still in L2.  The slab count is chosen from the node count
+ * (LBM_WAVE_SLABS overrides it).  Results are those of the split schedule,
+ * bit for bit; steps outside a graph run the split passes.
+ *
+ * LBM_KERNEL_PUSH (FP32 storage, single lattices): no density pass.  The
+ * collide-stream pass adds every post-collision population into the density
+ * accumulator of the node it streams into (integer fixed point with a
+ * resolution of 2^-26, so the sums are independent of the order of the
+ * atomic adds and the results are bitwise reproducible); a plane pass then
+ * applies the open-plane rule and sets the plane nodes' densities, and the
+ * wall pass follows.  The force stencil reads these densities, which differ
+ * from FP32 sums by at most a few units of 2^-26.  Graphs replay six steps. */
 
 /* Autotuner: times a few steps of the context's own lattice (or batch) at
  * each candidate block size of the split schedule (64, 128, 256 threads),

@@ -58,6 +58,11 @@ struct lbm_ctx {
     double *d_frozen = nullptr;
     int *h_flag = nullptr;  // pinned, device-mapped status word
     int *d_flag = nullptr;
+    // push schedule: rotating density accumulators, fluid-neighbour masks, and
+    // the step whose densities acc[step % 3] holds (-1: none)
+    unsigned long long *acc[3] = {nullptr, nullptr, nullptr};
+    uint32_t *d_nmask = nullptr;
+    int64_t push_step = -1;
     double mass0[2] = {0, 0};
     cudaEvent_t ev[kNumTimed + 1];
     bool have_ev = false;
@@ -76,6 +81,13 @@ struct lbm_ctx {
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;
     int64_t graph_launches = 0;  // kernels per replay
+    int graph_steps = 2;         // steps per replay
+    // wavefront schedule: per-plane prefix counts of fluid nodes and walls,
+    // slab boundaries (z planes), and the capture streams / events
+    std::vector<int> plane_n, plane_w, slab_z;
+    bool per_z = false;  // z periodic: the first and last slabs are neighbours
+    std::vector<cudaStream_t> wave_streams;
+    std::vector<cudaEvent_t> wave_events;
     size_t f_bytes = 0, rest_bytes = 0, bc_bytes = 0;  // the state a step reads and writes
     std::vector<uint8_t> solid_host;  // the mask, for host-side statistics
     // recording for the reverse pass (lbm_record / lbm_adjoint)
@@ -251,6 +263,7 @@ void touch(lbm_ctx *c)
 {
     c->graph_dirty = true;
     c->rec.valid = false;
+    c->push_step = -1;
     if (c->parent) {
         c->parent->states_dirty = true;
         c->parent->graph_dirty = true;
@@ -288,12 +301,51 @@ lbm_status capture_initial_mass(lbm_ctx *c)
     return LBM_OK;
 }
 
+// Push schedule: the accumulator of the current step from a density and wall
+// pass (any state), and a cleared accumulator for the next step.
+void push_prime_ctx(lbm_ctx *c)
+{
+    if (c->push_step == c->step) return;
+    const int par = (int)(c->step & 1);
+    Ops<float>::dens(c->s, par, c->step > 0, c->stream, c->block);
+    Ops<float>::wall(c->s, c->stream, c->block);
+    push_prime(c->s, c->acc[c->step % 3], c->stream);
+    cudaMemsetAsync(c->acc[(c->step + 1) % 3], 0, (size_t)c->nv * 8, c->stream);
+    c->launches += 3;
+    c->push_step = c->step;
+}
+
 // One time step of the split schedule.  ev != nullptr records events around
 // the kernels for lbm_step_timed.
 void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
 {
     const int par = (int)(c->step & 1);
     cudaStream_t st = c->stream;
+    if (c->kernel == LBM_KERNEL_PUSH) {
+        push_prime_ctx(c);
+        PushBufs pb;
+        pb.rd = c->acc[c->step % 3];
+        pb.acc = c->acc[(c->step + 1) % 3];
+        pb.clr = c->acc[(c->step + 2) % 3];
+        pb.nmask = c->d_nmask;
+        if (ev) cudaEventRecord(ev[0], st);
+        push_fused(c->s, pb, par, st);
+        if (ev) cudaEventRecord(ev[1], st);
+        push_plane(c->s, pb.acc, 1 - par, st);
+        if (ev) cudaEventRecord(ev[2], st);
+        push_wall(c->s, pb.acc, st);
+        if (ev) cudaEventRecord(ev[3], st);
+        c->launches += 1 + (c->s.open_z ? 1 : 0) + (c->s.n_wall > 0 ? 1 : 0);
+        c->step++;
+        c->push_step = c->step;
+        if (c->p.reduce_every > 0 && c->step % c->p.reduce_every == 0) {
+            run_reduce(c);
+            k_check<<<1, 1, 0, st>>>(c->d_red, c->mass0[0], c->mass0[1], c->p.drift_limit, c->s.open_z ? 0 : 1,
+                                     c->d_flag);
+            c->launches += 1;
+        }
+        return;
+    }
     if (c->kernel == LBM_KERNEL_FUSED) {
         PipeState &ps = c->ps;
         ps.epoch = (int)(c->pipe_launches + 1);
@@ -419,6 +471,32 @@ void step_once(lbm_ctx *c)
 
 // Capture two steps (even parity, after the first step) into a CUDA graph on a
 // private stream; the graph is then launched on the context's stream.
+// Slab boundaries (z planes) for the wavefront schedule: contiguous groups of
+// at least two planes with about equal fluid-node counts.  Fewer than three
+// slabs: no wavefront (empty).
+std::vector<int> plan_slabs(const lbm_ctx *c)
+{
+    const int nz = c->nz;
+    const int64_t N = c->s.n_fluid;
+    int K = std::max(1, (int)std::min<int64_t>(16, (N + 65535) / 65536));
+    if (const char *e = std::getenv("LBM_WAVE_SLABS")) K = std::max(1, std::atoi(e));
+    K = std::min(K, nz / 2);
+    std::vector<int> z{0};
+    if (K < 3) return {};
+    for (int k = 1; k < K; ++k) {
+        const int64_t target = N * k / K;
+        int zz = z.back() + 2;
+        while (zz < nz - 2 && c->plane_n[(size_t)zz] < target) ++zz;
+        if (zz > nz - 2) break;
+        z.push_back(zz);
+    }
+    z.push_back(nz);
+    if ((int)z.size() - 1 < 3) return {};
+    return z;
+}
+
+lbm_status capture_wave(lbm_ctx *c);
+
 lbm_status ensure_graph(lbm_ctx *c)
 {
     if (c->graph && !c->graph_dirty) return LBM_OK;
@@ -428,20 +506,25 @@ lbm_status ensure_graph(lbm_ctx *c)
     }
     if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
         return cuda_fail(c, cudaGetLastError(), "graph stream");
+    if (c->kernel == LBM_KERNEL_WAVE && c->subs.empty()) {
+        c->slab_z = plan_slabs(c);
+        if (!c->slab_z.empty()) return capture_wave(c);
+    }
+    c->graph_steps = c->kernel == LBM_KERNEL_PUSH ? 6 : 2;
     const cudaStream_t user = c->stream;
     const int64_t step0 = c->step, launches0 = c->launches;
     std::vector<int64_t> sub_steps;
     for (lbm_ctx *q : c->subs) sub_steps.push_back(q->step);
     c->stream = c->cap_stream;
+    const int64_t push0 = c->push_step;
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) {
-        step_once(c);
-        step_once(c);
-    }
+    if (e == cudaSuccess)
+        for (int q = 0; q < c->graph_steps; ++q) step_once(c);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &g) : e;
     c->stream = user;
     c->step = step0;
+    c->push_step = push0;
     for (size_t k = 0; k < c->subs.size(); ++k) c->subs[k]->step = sub_steps[k];
     c->graph_launches = c->launches - launches0;
     c->launches = launches0;
@@ -451,6 +534,133 @@ lbm_status ensure_graph(lbm_ctx *c)
         c->graph = nullptr;
         return cuda_fail(c, e2, "graph capture");
     }
+    c->graph_dirty = false;
+    return LBM_OK;
+}
+
+// The wavefront graph: G steps of density / wall / collide-stream passes per
+// slab, each launched on its own capture stream after the events of the
+// passes it reads (one stream per pass kind and slab, so stream order adds no
+// dependency that the data does not have).
+lbm_status capture_wave(lbm_ctx *c)
+{
+    const int K = (int)c->slab_z.size() - 1;
+    int G = 4;
+    if (const char *e = std::getenv("LBM_WAVE_STEPS")) G = std::max(2, std::atoi(e) & ~1);
+    // lag: density(t, k) also waits for collide-stream(t, k - L), which keeps
+    // about L slabs in flight so that a slab's populations are still in L2
+    // when its collide-stream pass reads them again (0: no such edge)
+    int L = 3;
+    if (const char *e = std::getenv("LBM_WAVE_LAG")) L = std::max(0, std::atoi(e));
+    const bool per_z = c->per_z;
+    auto nb = [&](int k, int d) {  // neighbour slab k + d, or -1
+        int q = k + d;
+        if (q < 0 || q >= K) {
+            if (!per_z) return -1;
+            q = (q + K) % K;
+        }
+        return q;
+    };
+    while ((int)c->wave_streams.size() < 3 * K) {
+        cudaStream_t st;
+        if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess)
+            return cuda_fail(c, cudaGetLastError(), "wave streams");
+        c->wave_streams.push_back(st);
+    }
+    while ((int)c->wave_events.size() < 3 * K * G + 1) {
+        cudaEvent_t ev;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess)
+            return cuda_fail(c, cudaGetLastError(), "wave events");
+        c->wave_events.push_back(ev);
+    }
+    auto EV = [&](int t, int kind, int k) { return c->wave_events[(size_t)1 + ((size_t)t * 3 + kind) * K + k]; };
+    auto ST = [&](int kind, int k) { return c->wave_streams[(size_t)kind * K + k]; };
+    const cudaStream_t cap = c->cap_stream;
+    const int64_t launches0 = c->launches;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaEventRecord(c->wave_events[0], cap);
+        for (int i = 0; i < 3 * K; ++i) cudaStreamWaitEvent(c->wave_streams[(size_t)i], c->wave_events[0], 0);
+        for (int t = 0; t < G; ++t) {
+            const int64_t step = c->step + t;
+            const int par = (int)(step & 1);
+            dispatch(c, [&](auto tag) {
+                using TS = decltype(tag);
+                auto dens = [&](int k) {
+                    cudaStream_t st = ST(0, k);
+                    if (t > 0)
+                        for (int d = -1; d <= 1; ++d)
+                            if (nb(k, d) >= 0) cudaStreamWaitEvent(st, EV(t - 1, 2, nb(k, d)), 0);
+                    if (!per_z && L >= 3 && k >= L) cudaStreamWaitEvent(st, EV(t, 2, k - L), 0);
+                    const int n0 = c->plane_n[(size_t)c->slab_z[(size_t)k]];
+                    const int n1 = c->plane_n[(size_t)c->slab_z[(size_t)k + 1]];
+                    Ops<TS>::dens(c->s, par, step > 0, st, c->block, n0, n1);
+                    c->launches += n1 > n0;
+                    cudaEventRecord(EV(t, 0, k), st);
+                };
+                auto wall = [&](int k) {
+                    cudaStream_t st = ST(1, k);
+                    for (int d = -1; d <= 1; ++d)
+                        if (nb(k, d) >= 0) cudaStreamWaitEvent(st, EV(t, 0, nb(k, d)), 0);
+                    const int w0 = c->plane_w[(size_t)c->slab_z[(size_t)k]];
+                    const int w1 = c->plane_w[(size_t)c->slab_z[(size_t)k + 1]];
+                    Ops<TS>::wall(c->s, st, c->block, w0, w1);
+                    c->launches += w1 > w0;
+                    cudaEventRecord(EV(t, 1, k), st);
+                };
+                auto fused = [&](int k) {
+                    cudaStream_t st = ST(2, k);
+                    for (int d = -1; d <= 1; ++d)
+                        if (nb(k, d) >= 0) {
+                            cudaStreamWaitEvent(st, EV(t, 0, nb(k, d)), 0);
+                            cudaStreamWaitEvent(st, EV(t, 1, nb(k, d)), 0);
+                        }
+                    const int n0 = c->plane_n[(size_t)c->slab_z[(size_t)k]];
+                    const int n1 = c->plane_n[(size_t)c->slab_z[(size_t)k + 1]];
+                    Ops<TS>::fused(c->s, par, st, c->block, n0, n1);
+                    c->launches += n1 > n0;
+                    cudaEventRecord(EV(t, 2, k), st);
+                };
+                // emission order must be a topological order of the edges.
+                // Open z: density k, wall k-1, collide-stream k-2 (wall k-1
+                // needs densities up to k; collide-stream k-2 needs walls up to
+                // k-1), so collide-stream k-L exists before density k for L >= 3.
+                // Periodic z: the first and last slabs depend on each other;
+                // all densities, then all walls, then all collide-streams.
+                if (!per_z) {
+                    for (int k = 0; k < K; ++k) {
+                        dens(k);
+                        if (k >= 1) wall(k - 1);
+                        if (k >= 2) fused(k - 2);
+                    }
+                    wall(K - 1);
+                    fused(K - 2);
+                    fused(K - 1);
+                } else {
+                    for (int k = 0; k < K; ++k) dens(k);
+                    for (int k = 0; k < K; ++k) wall(k);
+                    for (int k = 0; k < K; ++k) fused(k);
+                }
+            });
+        }
+        // join every capture stream back into the origin stream
+        for (int i = 0; i < 3 * K; ++i) {
+            cudaEventRecord(EV(G - 1, i / K, i % K), c->wave_streams[(size_t)i]);
+            cudaStreamWaitEvent(cap, EV(G - 1, i / K, i % K), 0);
+        }
+    }
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(cap, &g) : e;
+    c->graph_launches = c->launches - launches0;
+    c->launches = launches0;
+    if (e2 == cudaSuccess) e2 = cudaGraphInstantiate(&c->graph, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+        c->graph = nullptr;
+        cudaGetLastError();
+        return cuda_fail(c, e2, "wave graph capture");
+    }
+    c->graph_steps = G;
     c->graph_dirty = false;
     return LBM_OK;
 }
@@ -465,6 +675,8 @@ void destroy_ctx(lbm_ctx *c)
     for (lbm_ctx *q : c->subs) destroy_ctx(q);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (cudaStream_t st : c->wave_streams) cudaStreamDestroy(st);
+    for (cudaEvent_t ev : c->wave_events) cudaEventDestroy(ev);
     free_record(c);
     std::vector<std::pair<void *, size_t>> a = c->allocs;
     for (auto &q : a) dfree(c, q.first);
@@ -627,6 +839,7 @@ lbm_status tune(lbm_ctx *c, int *best)
         lbm_ctx *q = lat[k];
         dfree(q, saved[k].buf);
         q->step = saved[k].step;
+        q->push_step = -1;
         if (q->h_flag) *q->h_flag = saved[k].flag;
     }
     c->step = step0;
@@ -830,6 +1043,18 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         wxi.push_back(g->xi_field ? (double)g->xi_field[v] : p->xi);
     }
     const int64_t NW = (int64_t)wpvox.size();
+    // first node / wall of every z plane (both lists are in voxel order)
+    std::vector<int> plane_n((size_t)nz + 1, 0), plane_w((size_t)nz + 1, 0);
+    {
+        size_t a = 0, b = 0;
+        for (int z = 0; z <= nz; ++z) {
+            const int64_t v0 = (int64_t)z * nx * ny;
+            while (a < pvox.size() && (int64_t)pvox[a] < v0) ++a;
+            while (b < wpvox.size() && (int64_t)wpvox[b] < v0) ++b;
+            plane_n[(size_t)z] = (int)a;
+            plane_w[(size_t)z] = (int)b;
+        }
+    }
     if (18 * (((N + 63) / 64) * 64 + 64) >= ((int64_t)1 << 31))
         return fail(nullptr, LBM_ERR_UNSUPPORTED, "more than 113 million fluid nodes in one context");
 
@@ -846,7 +1071,14 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     c->open_axis = g->open_axis;
     c->p = *p;
     c->storage = p->storage;
-    c->kernel = p->kernel == LBM_KERNEL_FUSED ? LBM_KERNEL_FUSED : LBM_KERNEL_SPLIT;
+    c->kernel = p->kernel == LBM_KERNEL_FUSED ? LBM_KERNEL_FUSED
+                : p->kernel == LBM_KERNEL_WAVE    ? LBM_KERNEL_WAVE
+                : p->kernel == LBM_KERNEL_PUSH    ? LBM_KERNEL_PUSH
+                                                  : LBM_KERNEL_SPLIT;
+    if (c->kernel == LBM_KERNEL_PUSH && c->storage != LBM_STORE_FP32) {
+        delete c;
+        return fail(nullptr, LBM_ERR_UNSUPPORTED, "the push schedule needs FP32 storage");
+    }
 
     const size_t sz = p->storage == LBM_STORE_FP64 ? 8 : (is16(p->storage) ? 2 : 4);  // stored element bytes
     const size_t szc = p->storage == LBM_STORE_FP64 ? 8 : 4;                            // compute-type bytes
@@ -878,6 +1110,9 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     s.rref1 = p->rho_ref[0];
     s.rref2 = p->rho_ref[1];
     c->solid_host.assign(solid, solid + nv);
+    c->per_z = per[2] != 0;
+    c->plane_n = std::move(plane_n);
+    c->plane_w = std::move(plane_w);
     s.velocity_shift = p->velocity_shift ? 1 : 0;
 
     bool ok = true;
@@ -905,6 +1140,26 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     }
     c->d_partials = (double *)A((size_t)kReduceBlocks * kReduceSlots * 8);
     c->d_red = (double *)A((size_t)kReduceSlots * 8);
+    std::vector<uint32_t> nmask;
+    if (c->kernel == LBM_KERNEL_PUSH) {
+        for (int q = 0; q < 3; ++q) c->acc[q] = (unsigned long long *)A((size_t)nv * 8);
+        c->d_nmask = (uint32_t *)A((size_t)N * 4);
+        nmask.assign((size_t)N, 0u);
+        for (int64_t n = 0; n < N; ++n) {
+            const int64_t v = pvox[(size_t)n];
+            const int cc[3] = {(int)(v % nx), (int)((v / nx) % ny), (int)(v / ((int64_t)nx * ny))};
+            for (int j = 1; j < 19; ++j) {
+                int m[3] = {cc[0] + kEx[j], cc[1] + kEy[j], cc[2] + kEz[j]};
+                bool in = true;
+                for (int a = 0; a < 3; ++a)
+                    if (m[a] < 0 || m[a] >= dims[a]) {
+                        if (!per[a]) in = false;
+                        m[a] = (m[a] + dims[a]) % dims[a];
+                    }
+                if (in && !solid[m[0] + (int64_t)nx * (m[1] + (int64_t)ny * m[2])]) nmask[(size_t)n] |= 1u << j;
+            }
+        }
+    }
 
     // Single-pass schedule: chunk dependencies.  D of chunk c reads the
     // post-stream populations of its nodes, written by F of their fluid
@@ -999,6 +1254,7 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     };
     H2D(d_pvox, pvox.data(), (size_t)N * 4);
     H2D(d_nflags, nflags.data(), (size_t)N);
+    if (c->d_nmask) H2D(c->d_nmask, nmask.data(), (size_t)N * 4);
     H2D(d_cidx, cidx.data(), (size_t)nv * 4);
     H2D(d_wpvox, wpvox.data(), (size_t)NW * 4);
     H2D(d_wmask, wmask.data(), (size_t)NW * 4);
@@ -1163,19 +1419,24 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
         }
     }
     int64_t k = 0;
-    const bool graphs = c->kernel == LBM_KERNEL_SPLIT && !any_reduce(c) && n >= 4 &&
+    if (c->kernel == LBM_KERNEL_PUSH && n > 0) push_prime_ctx(c);
+    const int align = c->kernel == LBM_KERNEL_PUSH ? 6 : 2;
+    const bool graphs = c->kernel != LBM_KERNEL_FUSED && !any_reduce(c) && n >= 2 * align &&
                         std::getenv("LBM_NO_GRAPH") == nullptr;
     if (graphs) {
-        // the first step (no plane extrapolation yet) and odd parities run plain
-        while (k < n && (cur_step(c) == 0 || (cur_step(c) & 1))) {
+        // the first step (no plane extrapolation yet) and steps off the
+        // graph's period (parity; accumulator rotation) run plain
+        while (k < n && (cur_step(c) == 0 || cur_step(c) % align != 0)) {
             step_once(c);
             ++k;
         }
         if (n - k >= 2 && ensure_graph(c) == LBM_OK) {
-            for (; n - k >= 2; k += 2) {
+            const int gs = c->graph_steps;
+            for (; n - k >= gs; k += gs) {
                 cudaGraphLaunch(c->graph, c->stream);
-                c->step += 2;
-                for (lbm_ctx *q : c->subs) q->step += 2;
+                c->step += gs;
+                if (c->kernel == LBM_KERNEL_PUSH) c->push_step = c->step;
+                for (lbm_ctx *q : c->subs) q->step += gs;
                 c->launches += c->graph_launches;
             }
         }
@@ -1249,8 +1510,20 @@ lbm_status lbm_step_timed(lbm_ctx *c, int64_t n, double *kernel_ms, int32_t nk)
         for (auto &ev : c->ev) cudaEventCreate(&ev);
         c->have_ev = true;
     }
+    if (c->kernel == LBM_KERNEL_PUSH) push_prime_ctx(c);
     for (int64_t k = 0; k < n; ++k) {
         enqueue_step(c, c->ev);
+        if (c->kernel == LBM_KERNEL_PUSH) {  // collide-stream, plane, wall
+            cudaError_t e = cudaEventSynchronize(c->ev[3]);
+            if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_timed");
+            const int slot[3] = {2, 3, 1};
+            for (int q = 0; q < 3; ++q) {
+                float ms = 0;
+                cudaEventElapsedTime(&ms, c->ev[q], c->ev[q + 1]);
+                if (slot[q] < nk) kernel_ms[slot[q]] += ms;
+            }
+            continue;
+        }
         const bool fused = c->kernel == LBM_KERNEL_FUSED;
         cudaError_t e = cudaEventSynchronize(c->ev[fused ? 1 : 4]);
         if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_timed");

@@ -91,10 +91,12 @@ struct PipeState {
 // translation unit per storage type.
 template <typename TS>
 struct Ops {
-    // densities into psi; neem != 0 first applies the open-plane extrapolation
-    static void dens(const DevState &s, int parity, int neem, cudaStream_t st, int block = 256);
-    static void wall(const DevState &s, cudaStream_t st, int block = 256);
-    static void fused(const DevState &s, int parity, cudaStream_t st, int block = 256);
+    // densities into psi; neem != 0 first applies the open-plane extrapolation.
+    // [n0, n1) / [w0, w1): node / wall ranges (n1, w1 < 0: to the end)
+    static void dens(const DevState &s, int parity, int neem, cudaStream_t st, int block = 256, int n0 = 0,
+                     int n1 = -1);
+    static void wall(const DevState &s, cudaStream_t st, int block = 256, int w0 = 0, int w1 = -1);
+    static void fused(const DevState &s, int parity, cudaStream_t st, int block = 256, int n0 = 0, int n1 = -1);
     // the same three passes over many samples in one launch each: states[k] is
     // sample k; map[b] = (sample, block within the sample) for launch block b
     static void dens_batch(const DevState *states, const int2 *map, int nblocks, int parity, int neem,
@@ -120,6 +122,22 @@ struct Ops {
     // resident blocks per SM of the single-pass kernel
     static int pipe_blocks_per_sm();
 };
+
+// Push schedule (FP32 storage only, lbm_push.cu): the collide-stream pass
+// adds every post-collision population into the fixed-point density
+// accumulator of the node it streams into.
+struct PushBufs {
+    const unsigned long long *rd;  // densities of this step (dense, fluid and wall voxels)
+    unsigned long long *acc;       // next step's accumulators (cleared, fluid voxels)
+    unsigned long long *clr;       // the buffer to clear for the step after
+    const uint32_t *nmask;         // [n_fluid] bit j: x + e_j is an in-domain fluid voxel
+};
+void push_fused(const DevState &s, const PushBufs &pb, int parity, cudaStream_t st);
+// plane nodes after the pass: open-plane rule at the next parity, exact density
+void push_plane(const DevState &s, unsigned long long *acc, int parity_next, cudaStream_t st);
+void push_wall(const DevState &s, unsigned long long *acc, cudaStream_t st);
+// densities from the float psi of a density + wall pass (fluid and wall voxels)
+void push_prime(const DevState &s, unsigned long long *acc, cudaStream_t st);
 
 constexpr int kReduceBlocks = 1024;
 constexpr int kReduceThreads = 256;

@@ -528,18 +528,32 @@ __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb
 
 // neem = 0 skips the extrapolation (the state is an initial state that the
 // first step must see unchanged).
+// Plane node of the density pass: the open-plane rule, then the density read
+// back through L2 (the cells were just written by this thread; read-only
+// cache loads may be ordered before those writes).  Kept out of line so the
+// common path of the pass does not carry it.
 template <typename TS, int P>
-__device__ __forceinline__ void dens_pass_node(int t, const DevState &s, int neem)
+__device__ __noinline__ void dens_plane_node(int n, uint32_t pv, uint32_t fl, const DevState &s)
 {
     using C2 = typename Traits<TS>::C2;
-    if (t >= s.n_fluid) return;
-    const int n = s.n_fluid - 1 - t;
+    const int plane = (fl & F_INLET) ? 0 : 1;
+    const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
+    neem_node<TS, P, false>(plane, p, n, pv, fl, s);
+    const Nbr b = make_nbr(fl, s);
+    C2 f[19], dm;
+    load_pops<TS, P, true>(f, dm, n, pv, fl, b, s);
+    reinterpret_cast<C2 *>(s.psi)[pv] = density_of<TS>(dm, s);
+}
+
+template <typename TS, int P>
+__device__ __forceinline__ void dens_node_at(int n, const DevState &s, int neem)
+{
+    using C2 = typename Traits<TS>::C2;
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
     if (neem && (fl & (F_INLET | F_OUTLET))) {
-        const int plane = (fl & F_INLET) ? 0 : 1;
-        const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
-        neem_node<TS, P, false>(plane, p, n, pv, fl, s);
+        dens_plane_node<TS, P>(n, pv, fl, s);
+        return;
     }
     const Nbr b = make_nbr(fl, s);
     C2 f[19], dm;
@@ -548,9 +562,19 @@ __device__ __forceinline__ void dens_pass_node(int t, const DevState &s, int nee
 }
 
 template <typename TS, int P>
-__global__ void __launch_bounds__(256) k_dens(DevState s, int neem)
+__device__ __forceinline__ void dens_pass_node(int t, const DevState &s, int neem)
 {
-    dens_pass_node<TS, P>(blockIdx.x * blockDim.x + threadIdx.x, s, neem);
+    if (t >= s.n_fluid) return;
+    dens_node_at<TS, P>(s.n_fluid - 1 - t, s, neem);
+}
+
+// nodes [n0, n1), last first
+template <typename TS, int P>
+__global__ void __launch_bounds__(256) k_dens(DevState s, int neem, int n0, int n1)
+{
+    const int n = n1 - 1 - (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (n < n0) return;
+    dens_node_at<TS, P>(n, s, neem);
 }
 
 // Eq. 15 at one wall voxel: rho-tilde^sigma = chi^sigma * (sum of w_i rho^sigma
@@ -577,11 +601,12 @@ __device__ __forceinline__ void wall_node(int w, const DevState &s, void *psi_ou
     psi[pv] = mul2(acc, mk2((C(1) + xi) * inv, (C(1) - xi) * inv));
 }
 
+// walls [w0, w1)
 template <typename TS>
-__global__ void __launch_bounds__(256) k_wall(DevState s)
+__global__ void __launch_bounds__(256) k_wall(DevState s, int w0, int w1)
 {
-    const int w = blockIdx.x * blockDim.x + threadIdx.x;
-    if (w >= s.n_wall) return;
+    const int w = w0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (w >= w1) return;
     wall_node<TS, false>(w, s, s.psi);
 }
 
@@ -605,11 +630,12 @@ __device__ __forceinline__ void fused_node(int n, const DevState &s)
     store_pops<TS, P>(f, dm, n, pv, fl, b, s);
 }
 
+// nodes [n0, n1)
 template <typename TS, int P>
-__global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused(DevState s)
+__global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused(DevState s, int n0, int n1)
 {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= s.n_fluid) return;
+    const int n = n0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+    if (n >= n1) return;
     fused_node<TS, P>(n, s);
 }
 

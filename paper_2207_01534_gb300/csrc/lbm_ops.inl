@@ -7,26 +7,31 @@ namespace lbm {
 static inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 template <typename TS>
-void Ops<TS>::dens(const DevState &s, int parity, int neem, cudaStream_t st, int block)
+void Ops<TS>::dens(const DevState &s, int parity, int neem, cudaStream_t st, int block, int n0, int n1)
 {
-    if (s.n_fluid == 0) return;
-    if (parity) k_dens<TS, 1><<<grid_for(s.n_fluid, block), block, 0, st>>>(s, neem && s.open_z);
-    else k_dens<TS, 0><<<grid_for(s.n_fluid, block), block, 0, st>>>(s, neem && s.open_z);
+    if (n1 < 0) n1 = s.n_fluid;
+    if (n1 <= n0) return;
+    const unsigned g = grid_for(n1 - n0, block);
+    if (parity) k_dens<TS, 1><<<g, block, 0, st>>>(s, neem && s.open_z, n0, n1);
+    else k_dens<TS, 0><<<g, block, 0, st>>>(s, neem && s.open_z, n0, n1);
 }
 
 template <typename TS>
-void Ops<TS>::wall(const DevState &s, cudaStream_t st, int block)
+void Ops<TS>::wall(const DevState &s, cudaStream_t st, int block, int w0, int w1)
 {
-    if (s.n_wall == 0) return;
-    k_wall<TS><<<grid_for(s.n_wall, block), block, 0, st>>>(s);
+    if (w1 < 0) w1 = s.n_wall;
+    if (w1 <= w0) return;
+    k_wall<TS><<<grid_for(w1 - w0, block), block, 0, st>>>(s, w0, w1);
 }
 
 template <typename TS>
-void Ops<TS>::fused(const DevState &s, int parity, cudaStream_t st, int block)
+void Ops<TS>::fused(const DevState &s, int parity, cudaStream_t st, int block, int n0, int n1)
 {
-    if (s.n_fluid == 0) return;
-    if (parity) k_fused<TS, 1><<<grid_for(s.n_fluid, block), block, 0, st>>>(s);
-    else k_fused<TS, 0><<<grid_for(s.n_fluid, block), block, 0, st>>>(s);
+    if (n1 < 0) n1 = s.n_fluid;
+    if (n1 <= n0) return;
+    const unsigned g = grid_for(n1 - n0, block);
+    if (parity) k_fused<TS, 1><<<g, block, 0, st>>>(s, n0, n1);
+    else k_fused<TS, 0><<<g, block, 0, st>>>(s, n0, n1);
 }
 
 template <typename TS>

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(256, AdjOcc<TS>::blocks) k_adj_node(DevState s
     const C2 *psi = reinterpret_cast<const C2 *>(st.psi) + pv;
     const C2 rho = psi[0];
     C2 m[3] = {mk2(C(0), C(0)), mk2(C(0), C(0)), mk2(C(0), C(0))};
-    C2 lf = mul2(ls[0], ld_rest<TS, false>(st, n));
+    C2 lf = mul2(ls[0], ld_rest<TS, LD_NC>(st, n));
     {
         const S2 *M = reinterpret_cast<const S2 *>(st.f);
         const S2 *B = reinterpret_cast<const S2 *>(st.bc);

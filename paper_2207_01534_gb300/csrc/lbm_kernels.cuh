@@ -107,6 +107,20 @@ __device__ __forceinline__ C2 bc2(decltype(C2{}.x) k)  // (k, k)
 }
 
 // ---------------------------------------------------------------------------
+// Load modes for population and density reads: LD_NC through the read-only
+// cache (data the launch never writes), LD_CG through L2 only (data other
+// blocks of the same launch wrote), LD_CA an ordinary coherent load (data
+// this thread may have written earlier in the launch).
+enum : int { LD_NC = 0, LD_CG = 1, LD_CA = 2 };
+template <int LD, typename T>
+__device__ __forceinline__ T ldm(const T *p)
+{
+    if constexpr (LD == LD_NC) return __ldg(p);
+    else if constexpr (LD == LD_CG) return __ldcg(p);
+    else return *p;
+}
+
+// ---------------------------------------------------------------------------
 // Storage traits: how population pairs are kept in memory.  C / C2 are the
 // compute scalar and pair; S2 the stored pair of a moving population; R2 the
 // stored pair of the rest population.  ref is the per-direction offset
@@ -128,8 +142,8 @@ struct Traits<float> {
     __device__ static __forceinline__ S2 quant(C2 v, C2) { return v; }
     __device__ static __forceinline__ C2 dequant(S2 q, C2) { return q; }
     __device__ static __forceinline__ void store_q(S2 *p, S2 q) { *p = q; }
-    template <bool L2ONLY>
-    __device__ static __forceinline__ C2 load_dev(const S2 *p) { return L2ONLY ? __ldcg(p) : __ldg(p); }
+    template <int LD>
+    __device__ static __forceinline__ C2 load_dev(const S2 *p) { return ldm<LD>(p); }
     __device__ static __forceinline__ C2 code_value(S2 q) { return q; }
 };
 
@@ -147,8 +161,8 @@ struct Traits<double> {
     __device__ static __forceinline__ S2 quant(C2 v, C2) { return v; }
     __device__ static __forceinline__ C2 dequant(S2 q, C2) { return q; }
     __device__ static __forceinline__ void store_q(S2 *p, S2 q) { *p = q; }
-    template <bool L2ONLY>
-    __device__ static __forceinline__ C2 load_dev(const S2 *p) { return L2ONLY ? __ldcg(p) : __ldg(p); }
+    template <int LD>
+    __device__ static __forceinline__ C2 load_dev(const S2 *p) { return ldm<LD>(p); }
     __device__ static __forceinline__ C2 code_value(S2 q) { return q; }
 };
 
@@ -203,10 +217,10 @@ struct Traits16 {
         from_float(__fsub_rn(v, ref), h);
     }
     // the stored deviation itself, as FP32
-    template <bool L2ONLY>
+    template <int LD>
     __device__ static __forceinline__ C2 load_dev(const S2 *p)
     {
-        return unpack(L2ONLY ? __ldcg(reinterpret_cast<const unsigned *>(p)) : __ldg(reinterpret_cast<const unsigned *>(p)));
+        return unpack(ldm<LD>(reinterpret_cast<const unsigned *>(p)));
     }
     __device__ static __forceinline__ C2 code_value(S2 q) { return to_float2(q); }
 };
@@ -232,16 +246,16 @@ __device__ __forceinline__ typename Traits<TS>::C2 ref_of(const DevState &s, int
 // Rest-population pair of node n, kept at compute precision.  With deviation
 // storage the array holds f_0 - w_0 rho_ref (FP32); ld_rest returns f_0 and
 // ld_rest_dev the stored deviation.
-template <typename TS, bool L2ONLY>
+template <typename TS, int LD>
 __device__ __forceinline__ typename Traits<TS>::C2 ld_rest_dev(const DevState &s, int n)
 {
     const typename Traits<TS>::R2 *R = reinterpret_cast<const typename Traits<TS>::R2 *>(s.rest);
-    return L2ONLY ? __ldcg(R + n) : __ldg(R + n);
+    return ldm<LD>(R + n);
 }
-template <typename TS, bool L2ONLY>
+template <typename TS, int LD>
 __device__ __forceinline__ typename Traits<TS>::C2 ld_rest(const DevState &s, int n)
 {
-    const typename Traits<TS>::C2 v = ld_rest_dev<TS, L2ONLY>(s, n);
+    const typename Traits<TS>::C2 v = ld_rest_dev<TS, LD>(s, n);
     return Traits<TS>::kDev ? add2(v, ref_of<TS>(s, 0)) : v;
 }
 template <typename TS>
@@ -262,6 +276,15 @@ __device__ __forceinline__ typename Traits<TS>::C2 density_of(typename Traits<TS
     using C = typename Traits<TS>::C;
     return Traits<TS>::kDev ? add2(dm, mk2((C)s.rref1, (C)s.rref2)) : dm;
 }
+
+// ---------------------------------------------------------------------------
+// Programmatic dependent launch: a pass launched with the programmatic
+// serialization attribute may start while the previous pass finishes; it
+// waits for that pass (and the visibility of its writes) before its first
+// dependent read, and lets its own successor launch as soon as all of its
+// blocks are running.  Both are no-ops for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
 
 // ---------------------------------------------------------------------------
 // Geometry helpers
@@ -345,9 +368,10 @@ __device__ __forceinline__ C2 sum19(const C2 f[19])
 // deviation storage the deviation mass (rest deviation + sum of the stored
 // deviations), so that mass bookkeeping never adds the large common offsets
 // w_i rho_ref (whose identical rounding at every node would bias it); the
-// density is then density_of(dm) = rho_ref + dm.  L2ONLY loads bypass L1 (for
-// data written earlier in the same launch).
-template <typename TS, int P, bool L2ONLY = false>
+// density is then density_of(dm) = rho_ref + dm.  LD selects the load mode
+// (LD_CG for data other blocks of the launch wrote, LD_CA for data this
+// thread wrote).
+template <typename TS, int P, int LD = LD_NC>
 __device__ __forceinline__ void load_pops(typename Traits<TS>::C2 f[19], typename Traits<TS>::C2 &dm, int n,
                                           uint32_t pv, uint32_t fl, const Nbr &b, const DevState &s)
 {
@@ -356,7 +380,7 @@ __device__ __forceinline__ void load_pops(typename Traits<TS>::C2 f[19], typenam
     const S2 *M = reinterpret_cast<const S2 *>(s.f);
     const S2 *B = reinterpret_cast<const S2 *>(s.bc);
     const bool plane = P == 1 && (fl & (F_INLET | F_OUTLET));
-    const C2 r0 = ld_rest_dev<TS, L2ONLY>(s, n);
+    const C2 r0 = ld_rest_dev<TS, LD>(s, n);
     if (Traits<TS>::kDev) {
         dm = r0;
         f[0] = add2(r0, ref_of<TS>(s, 0));
@@ -367,12 +391,12 @@ __device__ __forceinline__ void load_pops(typename Traits<TS>::C2 f[19], typenam
     for (int j = 1; j < 19; ++j) {
         const S2 *p = (ez(j) != 0 && plane && outside(j, fl)) ? B + bc_cell(j, pv, fl, s)
                                                                : M + slot_in_block<P>(j, n, pv, b, s);
-        if (Traits<TS>::kDev) {
-            const C2 d = Traits<TS>::template load_dev<L2ONLY>(p);
+        if constexpr (Traits<TS>::kDev) {
+            const C2 d = Traits<TS>::template load_dev<LD>(p);
             dm = add2(dm, d);
             f[opp(j)] = add2(d, ref_of<TS>(s, j));
         } else {
-            f[opp(j)] = L2ONLY ? Traits<TS>::load_cg(p, ref_of<TS>(s, j)) : Traits<TS>::load(p, ref_of<TS>(s, j));
+            f[opp(j)] = ldm<LD>(p);  // plain storage: the stored pair itself
         }
     }
     if (!Traits<TS>::kDev) dm = sum19(f);
@@ -523,28 +547,16 @@ struct PipeOcc<double> {
 // open-plane extrapolation (idempotent: it only reads the interior node), then
 // every node sums its populations.  Nodes are taken in reverse order so the
 // pass starts on the lines the collide-stream kernel wrote last (still in L2).
-template <typename TS, int PN, bool L2ONLY>
+template <typename TS, int PN, int LD>
 __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb, uint32_t flb, const DevState &s);
 
 // neem = 0 skips the extrapolation (the state is an initial state that the
 // first step must see unchanged).
-// Plane node of the density pass: the open-plane rule, then the density read
-// back through L2 (the cells were just written by this thread; read-only
-// cache loads may be ordered before those writes).  Kept out of line so the
-// common path of the pass does not carry it.
-template <typename TS, int P>
-__device__ __noinline__ void dens_plane_node(int n, uint32_t pv, uint32_t fl, const DevState &s)
-{
-    using C2 = typename Traits<TS>::C2;
-    const int plane = (fl & F_INLET) ? 0 : 1;
-    const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
-    neem_node<TS, P, false>(plane, p, n, pv, fl, s);
-    const Nbr b = make_nbr(fl, s);
-    C2 f[19], dm;
-    load_pops<TS, P, true>(f, dm, n, pv, fl, b, s);
-    reinterpret_cast<C2 *>(s.psi)[pv] = density_of<TS>(dm, s);
-}
-
+// Density pass at node n: plane nodes first apply the open-plane rule, then
+// every node sums its populations.  The loads are ordinary coherent ones: a
+// plane node reads back cells it has just written (read-only cache loads may
+// be ordered before those writes), and one shared load path keeps the
+// common case as lean as before.
 template <typename TS, int P>
 __device__ __forceinline__ void dens_node_at(int n, const DevState &s, int neem)
 {
@@ -552,12 +564,13 @@ __device__ __forceinline__ void dens_node_at(int n, const DevState &s, int neem)
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
     if (neem && (fl & (F_INLET | F_OUTLET))) {
-        dens_plane_node<TS, P>(n, pv, fl, s);
-        return;
+        const int plane = (fl & F_INLET) ? 0 : 1;
+        const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
+        neem_node<TS, P, LD_NC>(plane, p, n, pv, fl, s);
     }
     const Nbr b = make_nbr(fl, s);
     C2 f[19], dm;
-    load_pops<TS, P>(f, dm, n, pv, fl, b, s);
+    load_pops<TS, P, LD_CA>(f, dm, n, pv, fl, b, s);
     reinterpret_cast<C2 *>(s.psi)[pv] = density_of<TS>(dm, s);
 }
 
@@ -572,6 +585,8 @@ __device__ __forceinline__ void dens_pass_node(int t, const DevState &s, int nee
 template <typename TS, int P>
 __global__ void __launch_bounds__(256) k_dens(DevState s, int neem, int n0, int n1)
 {
+    pdl_trigger();
+    pdl_wait();
     const int n = n1 - 1 - (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (n < n0) return;
     dens_node_at<TS, P>(n, s, neem);
@@ -579,7 +594,7 @@ __global__ void __launch_bounds__(256) k_dens(DevState s, int neem, int n0, int 
 
 // Eq. 15 at one wall voxel: rho-tilde^sigma = chi^sigma * (sum of w_i rho^sigma
 // over in-domain fluid neighbours) / (sum of those w_i), chi = 1 +/- xi.
-template <typename TS, bool L2ONLY>
+template <typename TS, int LD>
 __device__ __forceinline__ void wall_node(int w, const DevState &s, void *psi_out)
 {
     using C = typename Traits<TS>::C;
@@ -593,7 +608,7 @@ __device__ __forceinline__ void wall_node(int w, const DevState &s, void *psi_ou
     for (int j = 1; j < 19; ++j) {
         if (mask & (1u << j)) {
             const C2 *q = psi + ((int)pv + nb_off(j, b));
-            acc = fma2(bc2<C2>(wgt<C>(j)), L2ONLY ? __ldcg(q) : *q, acc);
+            acc = fma2(bc2<C2>(wgt<C>(j)), LD == LD_CG ? __ldcg(q) : *q, acc);
         }
     }
     const C inv = reinterpret_cast<const C *>(s.winv)[w];
@@ -605,9 +620,11 @@ __device__ __forceinline__ void wall_node(int w, const DevState &s, void *psi_ou
 template <typename TS>
 __global__ void __launch_bounds__(256) k_wall(DevState s, int w0, int w1)
 {
+    pdl_trigger();
+    pdl_wait();
     const int w = w0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (w >= w1) return;
-    wall_node<TS, false>(w, s, s.psi);
+    wall_node<TS, LD_NC>(w, s, s.psi);
 }
 
 // F: the fused force / collision / streaming update of one node.
@@ -634,6 +651,8 @@ __device__ __forceinline__ void fused_node(int n, const DevState &s)
 template <typename TS, int P>
 __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused(DevState s, int n0, int n1)
 {
+    pdl_trigger();
+    pdl_wait();
     const int n = n0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
     if (n >= n1) return;
     fused_node<TS, P>(n, s);
@@ -650,7 +669,7 @@ __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused(DevState s, 
 // momentum vanishes and f_i - f_opp(i) = 6 w_i rho_b u_n for the normal pair:
 // with j_n = rho_b - (in-plane sum + 2 outgoing sum) and N_t = half the
 // in-plane tangential momentum, f_i = f_opp(i) + 6 w_i j_n - e_i,t . N.
-template <typename TS, int PN, bool L2ONLY>
+template <typename TS, int PN, int LD>
 __device__ __forceinline__ void zou_he_node(int plane, int nb, uint32_t pvb, uint32_t flb, const DevState &s)
 {
     using C = typename Traits<TS>::C;
@@ -658,7 +677,7 @@ __device__ __forceinline__ void zou_he_node(int plane, int nb, uint32_t pvb, uin
     using S2 = typename Traits<TS>::S2;
     const Nbr bb = make_nbr(flb, s);
     C2 f[19], dm;
-    load_pops<TS, PN, L2ONLY>(f, dm, nb, pvb, flb, bb, s);
+    load_pops<TS, PN, LD>(f, dm, nb, pvb, flb, bb, s);
     const int pc = plane;               // prescribed component
     const int dir = plane == 0 ? 1 : -1;  // e_z of the entering directions
     C s0 = 0, sout = 0, nx = 0, ny = 0;
@@ -685,14 +704,14 @@ __device__ __forceinline__ void zou_he_node(int plane, int nb, uint32_t pvb, uin
     }
 }
 
-template <typename TS, int PN, bool L2ONLY>
+template <typename TS, int PN, int LD>
 __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb, uint32_t flb, const DevState &s)
 {
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
     using S2 = typename Traits<TS>::S2;
     if (s.zou_he) {
-        zou_he_node<TS, PN, L2ONLY>(plane, nb, pvb, flb, s);
+        zou_he_node<TS, PN, LD>(plane, nb, pvb, flb, s);
         // the other component's entering populations keep their initial values
         const Nbr bb = make_nbr(flb, s);
         const int qc = 1 - plane;
@@ -711,7 +730,7 @@ __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb
     const Nbr bi = make_nbr(fli, s);
     const Nbr bb = make_nbr(flb, s);
     C2 fi[19], dmi;
-    load_pops<TS, PN, L2ONLY>(fi, dmi, ni, pvi, fli, bi, s);
+    load_pops<TS, PN, LD>(fi, dmi, ni, pvi, fli, bi, s);
     const C2 r = density_of<TS>(dmi, s);
     C m[3] = {0, 0, 0};
 #pragma unroll
@@ -734,7 +753,7 @@ __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb
         const C fin = plane == 0 ? fi[i].x : fi[i].y;
         const C v = wgt<C>(i) * rb * base + fin - wgt<C>(i) * rin * base;
         if (i == 0) {
-            C2 rv = ld_rest<TS, L2ONLY>(s, nb);
+            C2 rv = ld_rest<TS, LD>(s, nb);
             if (pc == 0) rv.x = v; else rv.y = v;
             st_rest<TS>(s, nb, rv);
         } else {
@@ -762,7 +781,7 @@ __global__ void __launch_bounds__(128) k_plane(DevState s)
     const uint32_t pvb = plane == 0 ? (uint32_t)p : (uint32_t)(p + (s.nz - 1) * s.sxy);
     const int nb = s.cidx[pvb];
     if (nb < 0) return;
-    neem_node<TS, PN, false>(plane, p, nb, pvb, s.nflags[nb], s);
+    neem_node<TS, PN, LD_NC>(plane, p, nb, pvb, s.nflags[nb], s);
 }
 
 // ---------------------------------------------------------------------------
@@ -797,7 +816,7 @@ __global__ void __launch_bounds__(256) k_wall_batch(const DevState *states, cons
     const int2 m = map[blockIdx.x];
     const DevState &s = stage_state(states, m.x, &sh);
     const int w = m.y * blockDim.x + threadIdx.x;
-    if (w < s.n_wall) wall_node<TS, false>(w, s, s.psi);
+    if (w < s.n_wall) wall_node<TS, LD_NC>(w, s, s.psi);
 }
 
 template <typename TS, int P>

@@ -85,11 +85,11 @@ __device__ __forceinline__ void dens_node(int n, const DevState &s, void *psi_ne
     if (fl & (F_INLET | F_OUTLET)) {
         const int plane = (fl & F_INLET) ? 0 : 1;
         const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
-        neem_node<TS, PN, true>(plane, p, n, pv, fl, s);
+        neem_node<TS, PN, LD_CG>(plane, p, n, pv, fl, s);
     }
     const Nbr b = make_nbr(fl, s);
     C2 f[19], dm;
-    load_pops<TS, PN, true>(f, dm, n, pv, fl, b, s);
+    load_pops<TS, PN, LD_CG>(f, dm, n, pv, fl, b, s);
     reinterpret_cast<C2 *>(psi_next)[pv] = density_of<TS>(dm, s);
 }
 
@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(kChunk, PipeOcc<TS>::blocks) k_pipe(DevState s
                 if (need >= 0 && !wait_round(ps.round_d, need / G, full, ps)) return;
                 // this warp's share of the wall chunk
                 for (int w = ps.wstart[cw] + threadIdx.x; w < ps.wstart[cw + 1]; w += kChunk)
-                    wall_node<TS, true>(w, s, ps.psi_next);
+                    wall_node<TS, LD_CG>(w, s, ps.psi_next);
             }
         }
     }

@@ -131,12 +131,12 @@ __global__ void __launch_bounds__(128) k_plane_push(DevState s, unsigned long lo
     const int nb = s.cidx[pvb];
     if (nb < 0) return;
     const uint32_t flb = s.nflags[nb];
-    neem_node<TS, PN, false>(plane, p, nb, pvb, flb, s);
+    neem_node<TS, PN, LD_NC>(plane, p, nb, pvb, flb, s);
     const Nbr bb = make_nbr(flb, s);
     float2 f[19], dm;
     // read back through L2: the cells were just written by this thread, and
     // the read-only cache is not coherent with those writes
-    load_pops<TS, PN, true>(f, dm, nb, pvb, flb, bb, s);
+    load_pops<TS, PN, LD_CA>(f, dm, nb, pvb, flb, bb, s);
     acc[pvb] = fix_total2(dm);
 }
 

@@ -581,9 +581,21 @@ __device__ __forceinline__ void dens_pass_node(int t, const DevState &s, int nee
     dens_node_at<TS, P>(s.n_fluid - 1 - t, s, neem);
 }
 
+// Resident blocks per SM of the density pass: four for FP32 and 16-bit
+// storage (the odd-parity gather otherwise takes 80 registers and three
+// blocks: 39.7 vs 36.8 us per pass on the 128^3 pack), two for FP64.
+template <typename TS>
+struct DensOcc {
+    static constexpr int blocks = 4;
+};
+template <>
+struct DensOcc<double> {
+    static constexpr int blocks = 2;
+};
+
 // nodes [n0, n1), last first
 template <typename TS, int P>
-__global__ void __launch_bounds__(256) k_dens(DevState s, int neem, int n0, int n1)
+__global__ void __launch_bounds__(256, DensOcc<TS>::blocks) k_dens(DevState s, int neem, int n0, int n1)
 {
     pdl_trigger();
     pdl_wait();

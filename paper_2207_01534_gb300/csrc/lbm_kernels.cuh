@@ -191,23 +191,20 @@ struct Traits16 {
     __device__ static __forceinline__ S2 quant(C2 v, C2 ref)
     {
         S2 h;
-        from_float2(make_float2(__fsub_rn(v.x, ref.x), __fsub_rn(v.y, ref.y)), &h);
+        from_float2(sub2(v, ref), &h);  // one packed, explicitly rounded subtraction
         return h;
     }
     __device__ static __forceinline__ C2 dequant(S2 q, C2 ref)
     {
-        const float2 d = to_float2(q);
-        return make_float2(__fadd_rn(ref.x, d.x), __fadd_rn(ref.y, d.y));
+        return add2(ref, to_float2(q));
     }
     __device__ static __forceinline__ C2 load(const S2 *p, C2 ref)
     {
-        const float2 d = unpack(__ldg(reinterpret_cast<const unsigned *>(p)));
-        return make_float2(__fadd_rn(ref.x, d.x), __fadd_rn(ref.y, d.y));
+        return add2(ref, unpack(__ldg(reinterpret_cast<const unsigned *>(p))));
     }
     __device__ static __forceinline__ C2 load_cg(const S2 *p, C2 ref)
     {
-        const float2 d = unpack(__ldcg(reinterpret_cast<const unsigned *>(p)));
-        return make_float2(__fadd_rn(ref.x, d.x), __fadd_rn(ref.y, d.y));
+        return add2(ref, unpack(__ldcg(reinterpret_cast<const unsigned *>(p))));
     }
     __device__ static __forceinline__ void store(S2 *p, C2 v, C2 ref) { *p = quant(v, ref); }
     __device__ static __forceinline__ void store_q(S2 *p, S2 q) { *p = q; }
@@ -237,8 +234,9 @@ __device__ __forceinline__ typename Traits<TS>::C2 ref_of(const DevState &s, int
     if constexpr (!Traits<TS>::kDev) {
         return mk2(C(0), C(0));
     } else {
-        // explicitly rounded (never contracted into a later add), so every
-        // kernel that dequantises gets the same bits
+        // explicitly rounded scalar products (documented never to be merged
+        // into a multiply-add), so every kernel that dequantises gets the
+        // same bits
         return mk2(__fmul_rn(wgt<C>(i), (C)s.rref1), __fmul_rn(wgt<C>(i), (C)s.rref2));
     }
 }

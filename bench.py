@@ -422,7 +422,7 @@ def run_adjoint(args, rank, world):
     from paper_2207_01534_gb300 import lbm
 
     lbm.load()
-    nsteps, every = 500, 50
+    nsteps, every = args.adjoint_steps, min(args.checkpoint_every, args.adjoint_steps)
     nf = int((solid == 0).sum())
     kw = dict(tau=inputs.tau_for_viscosity_ratio(10.0), G=3.5, xi=inputs.xi_of_theta(45.0), periodic=(1, 1, 0),
               open_axis=2, rho_in1=_pc_inlet(pc=0.0), rho_out2=1.0, sample=(8, 88))
@@ -490,6 +490,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=(WORKLOAD, BATCH_WORKLOAD, ADJOINT_WORKLOAD))
     ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache (batched workload)")
+    ap.add_argument("--adjoint-steps", type=int, default=500, help="recorded steps (adjoint workload)")
+    ap.add_argument("--checkpoint-every", type=int, default=50, help="checkpoint interval (adjoint workload)")
     args = ap.parse_args()
     assert args.warmup >= 0 and args.steps > 0
     rank = int(os.environ.get("RANK", "0"))

@@ -314,6 +314,27 @@ def batched_sample(spec):
     return solid, r1, r2
 
 
+def rock_grf_256(seed_offset=3):
+    """256^3 sandstone stand-in: periodic Gaussian random field, correlation
+    length 6, thresholded to porosity 0.22, 8-slice reservoirs, drainage start."""
+    solid = grf_rock(256, 6.0, 0.22, SEED_BASE + seed_offset, reservoir=8)
+    r1, r2 = drainage_init(solid, 8)
+    return solid, r1, r2
+
+
+def crop(solid, n, reservoir=4, origin=None):
+    """An n^3 sub-block of a rock (from its centre unless ``origin`` (z, y, x) is
+    given) with ``reservoir`` fluid slices added at both z ends (inside the n
+    slices) and only percolating pores kept."""
+    nz, ny, nx = solid.shape
+    if origin is None:
+        origin = ((nz - n) // 2, (ny - n) // 2, (nx - n) // 2)
+    z, y, x = origin
+    c = solid[z:z + n, y:y + n, x:x + n].copy()
+    c = add_reservoirs(c, reservoir)
+    return keep_percolating(c, True)
+
+
 def adjoint_pack_96(seed_offset=2):
     """96^3 sphere pack, radius 6, porosity 0.40, 8-slice reservoirs, with the
     imbibition start (oil everywhere, water in the outlet reservoir)."""

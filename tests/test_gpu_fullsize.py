@@ -1,0 +1,151 @@
+"""The named configurations at full size, in the launch configuration the
+benchmark times: outputs the oracle can compute (one step from the GPU's own
+state), properties that hold at any size, and the comparisons each
+configuration names (16-bit vs FP32 and the oracle on a crop; the reverse
+pass vs a directional difference; batch members vs their solo runs)."""
+import numpy as np
+import pytest
+
+import bench
+import oracle
+from paper_2207_01534_gb300 import drivers, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+
+    assert torch.cuda.is_available(), "these tests need a GPU"
+    from paper_2207_01534_gb300 import lbm as m
+
+    m.load()
+    return m
+
+
+def test_drainage_pack_128_one_step_against_the_oracle(lbm):
+    """128^3 sphere pack (958,185 fluid nodes), the benchmark's lattice and
+    schedule: 200 steps (graph replays), then one more step on the GPU and in
+    the FP64 oracle from the GPU's state, every population compared."""
+    solid, r1, r2, kw, cfg = bench.workload_setup()
+    g = lbm.Lattice(solid, **kw)
+    g.init_densities(r1, r2)
+    m0 = g.saturation()
+    g.step(200)
+    f1, f2 = g.get_populations()
+    assert np.isfinite(f1).all() and np.isfinite(f2).all()
+    s = g.saturation()
+    assert 0.0 < s[0] <= 1.0 and 0.0 <= s[1] < 1.0 and s[2] > m0[2]  # oil is entering
+    o = oracle.Oracle(solid, **kw)
+    o.set_pops(f1, f2)  # the GPU's missing populations still hold their initial values
+    g.step(1)
+    o.step(1)
+    a1, a2 = g.get_populations()
+    b1, b2 = o.get_pops()
+    assert np.abs(a1 - b1).max() <= 2e-6 and np.abs(a2 - b2).max() <= 2e-6
+
+
+@pytest.fixture(scope="module")
+def rock256():
+    return inputs.rock_grf_256()
+
+
+def _rock_kw():
+    return dict(tau=inputs.tau_for_viscosity_ratio(10.0), G=3.5, xi=inputs.xi_of_theta(45.0), periodic=(1, 1, 0),
+                open_axis=2, rho_in1=drivers.inlet_density(0.02), rho_out2=1.0)
+
+
+def test_rock_256_sixteen_bit_against_fp32(lbm, rock256):
+    """256^3 random-field rock (porosity 0.22): FP16 / BF16 deviation storage
+    against the FP32 path after 400 steps (saturations of the sample slab)."""
+    solid, r1, r2 = rock256
+    kw = dict(_rock_kw(), sample=(8, 248))
+    out = {}
+    for storage in ("fp32", "fp16dev", "bf16dev"):
+        g = lbm.Lattice(solid, storage=storage, **kw)
+        g.init_densities(r1, r2)
+        g.step(400)
+        out[storage] = g.saturation()
+        g.close()
+    print({k: tuple(round(x, 5) for x in v[:2]) for k, v in out.items()})
+    assert out["fp32"][0] < 0.999  # the front has entered the sample
+    for storage, bound in (("fp16dev", 0.002), ("bf16dev", 0.01)):
+        assert abs(out[storage][0] - out["fp32"][0]) <= bound
+        assert abs(out[storage][1] - out["fp32"][1]) <= bound
+
+
+def test_rock_256_crop_against_the_oracle(lbm, rock256):
+    """A 64^3 crop of the same rock with 4-slice reservoirs: FP32 at the
+    parity bound and 16-bit storage within bounds set from its measured error
+    with a margin of about two (a front moving through a rock moves the
+    interface nodes, so the L-infinity density error is larger than for the
+    static droplet), against the FP64 oracle after 300 steps."""
+    solid = inputs.crop(rock256[0], 64, reservoir=4)
+    r1, r2 = inputs.drainage_init(solid, 4)
+    kw = _rock_kw()
+    o = oracle.Oracle(solid, **kw)
+    o.init_densities(r1, r2)
+    o.step(300)
+    fo = o.fields()
+    for storage, tol in (("fp32", 1e-5), ("fp16dev", 1e-2), ("bf16dev", 5e-2)):  # measured 2e-6, 5.3e-3, 2.2e-2
+        g = lbm.Lattice(solid, storage=storage, **kw)
+        g.init_densities(r1, r2)
+        g.step(300)
+        fg = g.fields(("rho1", "rho2"))
+        e = max(np.abs(fg[k] - fo[k]).max() / np.abs(fo[k]).max() for k in ("rho1", "rho2"))
+        print(storage, "rel L-inf %.2e" % e)
+        assert e <= tol
+
+
+def test_adjoint_pack_96_directional_derivative(lbm):
+    """The 96^3 adjoint configuration (500 steps, checkpoints every 50, FP32):
+    the gradient along a random direction of (xi field, inlet density) against
+    a central difference of the FP64 forward (eps = 1e-3)."""
+    import torch
+
+    solid, r1, r2 = inputs.adjoint_pack_96()
+    kw = dict(tau=inputs.tau_for_viscosity_ratio(10.0), G=3.5, periodic=(1, 1, 0), open_axis=2,
+              rho_in1=drivers.inlet_density(0.0), rho_out2=1.0, sample=(8, 88))
+    xi = np.where(solid == 1, inputs.xi_of_theta(45.0), 0.0).astype(np.float32)
+    g = lbm.Lattice(solid, storage="fp32", **kw)
+    g.set_xi_field(xi)
+    g.init_densities(r1, r2)
+    g.record(500, 50)
+    gx = torch.zeros(solid.shape, dtype=torch.float32, device="cuda")
+    J, grin = g.adjoint(1.0, gx)
+    rng = np.random.default_rng(96)
+    dx = (rng.standard_normal(solid.shape) * (solid == 1)).astype(np.float32)
+    drin = 0.5
+    pred = float((gx.cpu().numpy().astype(np.float64) * dx).sum()) + grin * drin
+
+    def J_at(t):
+        h = lbm.Lattice(solid, storage="fp64", **dict(kw, rho_in1=kw["rho_in1"] + t * drin))
+        h.set_xi_field((xi + t * dx).astype(np.float32))
+        h.init_densities(r1, r2)
+        h.step(500)
+        return h.saturation()[1]
+
+    eps = 1e-3
+    fd = (J_at(eps) - J_at(-eps)) / (2 * eps)
+    print("J %.6f  directional: adjoint %.6e  central difference %.6e" % (J, pred, fd))
+    assert abs(fd) > 1e-7
+    assert abs(pred - fd) <= 1e-2 * abs(fd)
+
+
+def test_batched_sweep_64_members_equal_their_solo_runs(lbm):
+    """The 64-sample sweep as one batch: three members (smallest, largest,
+    one in between) are bitwise their solo runs after 12 steps."""
+    samples, states, cfg = bench.batch_setup()
+    b = lbm.Batch([dict(kw) for kw in samples])
+    for smp, (r1, r2) in zip(b.samples, states):
+        smp.init_densities(r1, r2)
+    b.step(12)
+    sizes = [kw["solid"].size for kw in samples]
+    for k in (int(np.argmin(sizes)), int(np.argmax(sizes)), 17):
+        solo = lbm.Lattice(**dict(samples[k], kernel="split"))
+        solo.init_densities(*states[k])
+        solo.step(12)
+        a1, a2 = b[k].get_populations()
+        s1, s2 = solo.get_populations()
+        assert np.array_equal(a1, s1) and np.array_equal(a2, s2), k

@@ -290,6 +290,23 @@ lbm_status lbm_set_xi_field(lbm_ctx *ctx, const float *xi, int32_t on_device);
 lbm_status lbm_record(lbm_ctx *ctx, int64_t nsteps, int32_t every);
 lbm_status lbm_adjoint(lbm_ctx *ctx, double dloss, float *grad_xi, double *grad_rho_in1, double *loss);
 
+/* ---- Failure handling ----------------------------------------------------
+ * The single-pass schedule (LBM_KERNEL_FUSED) orders its blocks with device
+ * waits; each wait gives up after a time limit (default 1 s, measured with the
+ * GPU's global timer), sets an abort word that stops every block, and raises
+ * LBM_ERR_TIMEOUT from the next lbm_step / lbm_synchronize.  The kernel then
+ * returns normally: the context stays usable, the populations of the
+ * abandoned step are undefined, and the next initialisation (or
+ * lbm_set_populations) starts over; the schedule's counters are cleared
+ * before its next launch.
+ *
+ * lbm_set_wait_limit sets the limit (0 < seconds <= 60).  lbm_inject_stall
+ * makes the next single-pass step wait for a round that never completes, so
+ * that the timeout path can be tested without faulting or hanging the GPU
+ * (LBM_ERR_UNSUPPORTED for other schedules). */
+lbm_status lbm_set_wait_limit(lbm_ctx *ctx, double seconds);
+lbm_status lbm_inject_stall(lbm_ctx *ctx);
+
 /* Largest n accepted by lbm_saturation_static. */
 #define LBM_SATURATION_STATIC_MAX_N 16777216
 

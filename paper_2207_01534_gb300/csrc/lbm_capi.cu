@@ -106,6 +106,8 @@ struct lbm_ctx {
     void *psi_alt = nullptr;
     int pipe_grid = 0;
     int64_t pipe_launches = 0;
+    bool pipe_reset = false;  // a single-pass launch gave up: clear its counters before the next
+    bool stall_next = false;  // lbm_inject_stall: the next single-pass launch waits for nothing
 };
 
 namespace lbm {
@@ -253,7 +255,10 @@ lbm_status device_status(lbm_ctx *c)
     const int f = c->h_flag ? *(volatile int *)c->h_flag : 0;
     if (f & 1) return fail(c, LBM_ERR_NONFINITE, "non-finite density found by the periodic check");
     if (f & 2) return fail(c, LBM_ERR_DRIFT, "mass drift above drift_limit");
-    if (f & 4) return fail(c, LBM_ERR_TIMEOUT, "a bounded device wait gave up");
+    if (f & 4) {
+        c->pipe_reset = true;
+        return fail(c, LBM_ERR_TIMEOUT, "a bounded device wait gave up (populations undefined: reinitialise)");
+    }
     return LBM_OK;
 }
 
@@ -348,7 +353,15 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
     }
     if (c->kernel == LBM_KERNEL_FUSED) {
         PipeState &ps = c->ps;
-        ps.epoch = (int)(c->pipe_launches + 1);
+        if (c->pipe_reset) {  // counters of an abandoned launch: start over
+            cudaMemsetAsync(ps.round_f, 0, (size_t)ps.n_chunks * 8 * 16 * 8, st);
+            cudaMemsetAsync(ps.round_d, 0, (size_t)ps.n_chunks * 8 * 16 * 8, st);
+            cudaMemsetAsync(ps.abort, 0, 4, st);
+            c->pipe_launches = 0;
+            c->pipe_reset = false;
+        }
+        ps.epoch = (int)(c->pipe_launches + 1) + (c->stall_next ? (1 << 20) : 0);
+        c->stall_next = false;
         ps.psi_next = c->psi_alt;
         dispatch(c, [&](auto tag) {
             using TS = decltype(tag);
@@ -1225,6 +1238,7 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         ps.round_f = (unsigned long long *)A((size_t)NC * 8 * 16 * 8);
         ps.round_d = (unsigned long long *)A((size_t)NC * 8 * 16 * 8);
         ps.abort = (int *)A(4);
+        ps.wait_ns = 1000000000ull;  // one second
         c->psi_alt = A((size_t)nv * 2 * szc);
     }
     if (!ok) {
@@ -1884,6 +1898,22 @@ lbm_status lbm_adjoint(lbm_ctx *c, double dloss, float *grad_xi, double *grad_rh
     if (loss) *loss = J;
     stt = check_launch(c, "lbm_adjoint");
     return stt != LBM_OK ? stt : device_status(c);
+}
+
+lbm_status lbm_set_wait_limit(lbm_ctx *c, double seconds)
+{
+    if (!c || !(seconds > 0.0) || seconds > 60.0) return LBM_ERR_ARG;
+    c->ps.wait_ns = (unsigned long long)(seconds * 1e9);
+    return LBM_OK;
+}
+
+lbm_status lbm_inject_stall(lbm_ctx *c)
+{
+    if (!c) return LBM_ERR_ARG;
+    if (c->kernel != LBM_KERNEL_FUSED)
+        return fail(c, LBM_ERR_UNSUPPORTED, "only the single-pass schedule has device waits");
+    c->stall_next = true;
+    return LBM_OK;
 }
 
 const char *lbm_last_error(const lbm_ctx *c) { return c ? c->err.c_str() : g_create_err.c_str(); }

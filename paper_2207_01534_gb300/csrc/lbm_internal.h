@@ -63,7 +63,8 @@ struct DevState {
 // densities of wall chunk (r - lag_w)*G + b (W).  D waits for F of every chunk
 // up to need_f[c]; W for D up to need_d[c].  F never waits, and the lags make
 // every wait target a phase that is already done or running without waiting,
-// so the launch always finishes; waits are bounded anyway (kPipeMaxPolls).
+// so the launch always finishes; waits are bounded anyway (wait_ns of the
+// global timer, and kPipeMaxPolls polls as a backstop).
 // Completion frontiers are tagged with the launch epoch, so nothing is reset
 // between launches.
 constexpr int kChunk = 256;             // fluid nodes per chunk = threads per block
@@ -85,6 +86,7 @@ struct PipeState {
     void *psi_next;              // densities of the next step (the other psi buffer)
     int epoch;                   // 1 + launches of this schedule so far
     int n_chunks, n_rounds, lag_d, lag_w, rounds;
+    unsigned long long wait_ns;  // a wait gives up after this long (global timer)
 };
 
 // Per-storage-type kernel launchers, explicitly instantiated in one

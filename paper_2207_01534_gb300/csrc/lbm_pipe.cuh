@@ -10,8 +10,8 @@
 // Ordering.  Each warp counts itself into a round's completion counters after
 // its own stores and a device-scope fence; waiting warps read the counters
 // with acquire loads; data written in this launch is read
-// with L2-only loads.  Waits are bounded: after kPipeMaxPolls polls a block
-// sets the abort word and the timeout status bit, and every block stops.
+// with L2-only loads.  Waits are bounded: after ps.wait_ns (global timer) a
+// block sets the abort word and the timeout status bit, and every block stops.
 #pragma once
 
 #include "lbm_kernels.cuh"
@@ -43,17 +43,28 @@ __device__ __forceinline__ void st_release(int *p, int v)
 // every sub-counter has reached e * G.
 constexpr int kWarps = kChunk / 32;
 
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // Wait (one warp) until round `r` of counter array `ctr` is complete.
-// Returns false after a timeout or an abort (warp-uniform).
+// Returns false after a timeout (ps.wait_ns of the global timer, or
+// kPipeMaxPolls polls) or an abort by another block (warp-uniform).
 __device__ __forceinline__ bool wait_round(const unsigned long long *ctr, int r, unsigned long long target,
                                            const PipeState &ps)
 {
     const int lane = threadIdx.x & 31;
     int backoff = 32;
+    const unsigned long long t0 = __shfl_sync(0xffffffffu, global_ns(), 0);
     for (int it = 0; it < kPipeMaxPolls; ++it) {
         const bool mine = lane >= kWarps || ld_acquire64(ctr + 16 * (r * kWarps + lane)) >= target;
         if (__all_sync(0xffffffffu, mine)) return true;
         if (*(volatile int *)ps.abort) break;
+        const unsigned long long t = __shfl_sync(0xffffffffu, global_ns(), 0);
+        if (t - t0 > ps.wait_ns) break;
         __nanosleep(backoff);
         backoff = min(backoff * 2, 512);
     }

@@ -94,13 +94,15 @@ def load(build_if_missing: bool = True):
     lib.lbm_autotune.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]
     lib.lbm_set_xi_field.argtypes = [P, P, ctypes.c_int32]
     lib.lbm_record.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
+    lib.lbm_set_wait_limit.argtypes = [P, ctypes.c_double]
+    lib.lbm_inject_stall.argtypes = [P]
     lib.lbm_adjoint.argtypes = [P, ctypes.c_double, P, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double)]
     for name in ("lbm_default_params", "lbm_create", "lbm_set_allocator", "lbm_init_densities",
                  "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_step_timed", "lbm_read_fields",
                  "lbm_saturation", "lbm_saturation_static", "lbm_set_inlet", "lbm_set_stream", "lbm_synchronize",
                  "lbm_get_info", "lbm_create_batch", "lbm_batch_get", "lbm_autotune", "lbm_set_xi_field",
-                 "lbm_record", "lbm_adjoint"):
+                 "lbm_record", "lbm_adjoint", "lbm_set_wait_limit", "lbm_inject_stall"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -239,6 +241,14 @@ class Lattice:
         else:
             a = np.ascontiguousarray(np.broadcast_to(xi, self.shape), dtype=np.float32)
             self._c(self._lib.lbm_set_xi_field(self._h, a.ctypes.data, 0))
+
+    def set_wait_limit(self, seconds: float):
+        """lbm_set_wait_limit: time limit of the single-pass schedule's device waits."""
+        self._c(self._lib.lbm_set_wait_limit(self._h, float(seconds)))
+
+    def inject_stall(self):
+        """lbm_inject_stall: the next single-pass step waits for a round that never completes."""
+        self._c(self._lib.lbm_inject_stall(self._h))
 
     def record(self, nsteps: int, every: int = 50):
         """lbm_record: nsteps steps, keeping a checkpoint every ``every`` steps."""

@@ -48,6 +48,7 @@ ALGO_BYTES = {"fp32": 2 * (18 * 8 + 8) + 4, "fp64": 2 * (18 * 16 + 16) + 4,
               "fp16dev": 2 * (18 * 4 + 8) + 4, "bf16dev": 2 * (18 * 4 + 8) + 4}
 DTYPE = {"fp32": "f32", "fp64": "f64", "fp16dev": "f32 (f16 storage)", "bf16dev": "f32 (bf16 storage)"}
 WORKLOAD = "drainage_pack_128"
+NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
 
 def workload_setup():
@@ -278,6 +279,7 @@ def run_ours(args, rank, world):
     step_bytes_rate = algo * nf / (ms / args.steps / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": measured_traffic("k_fused"), "kernel": "k_fused", "peak_kind": peak_kind,
+            "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
             "algorithmic_bytes_per_node": algo, "kernel_ms": {names[k]: float(kms[k]) for k in range(5)},
             "step_frac": step_bytes_rate / peak}
     del lat
@@ -301,9 +303,16 @@ def run_ours(args, rank, world):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
         v, done, cdt = oracle_rate(solid, r1, r2, kw, steps=args.cpu_steps)
+        oracle.set_threads(1)
+        v1, done1, cdt1 = oracle_rate(solid, r1, r2, kw, steps=2, budget_s=15.0)
+        oracle.set_threads(os.cpu_count() or 1)
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "%d full steps of the %s workload (%.1f s)" % (done, WORKLOAD, cdt)}
+               "sample": "%d full steps of the %s workload (%.1f s); one core: %d steps (%.1f s)" % (
+                   done, WORKLOAD, cdt, done1, cdt1),
+               "value_one_core": v1}
     cfg = dict(cfg)
     cfg.update({"parallelism": "replicas" if world > 1 else "single", "kernel_schedule": args.kernel,
                 "storage": args.storage,

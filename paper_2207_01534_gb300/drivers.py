@@ -6,6 +6,8 @@ time step runs in liblbm's CUDA kernels).
 * ``pc_sw_curve``: the capillary-pressure ramp of Sections 4.1-4.2 -- the inlet
   density is raised stage by stage, each stage run until the water saturation
   settles, giving the P_c - S_w curve.
+* ``drainage_history``: S_w(t) and the trapped wetting volume every few
+  hundred steps of a drainage (Section 4.1 outputs).
 * ``contact_angle``: the flat-wall calibration of Section 3.2 at reduced size
   -- a cap of component 1 (oil) on a wall, relaxed, its angle measured through
   component 2 (water) from the base width a few lattice units above the wall
@@ -58,6 +60,39 @@ def pc_sw_curve(lattice, pcs, G=3.5, minor=0.03, rho_out2=1.0, max_steps=20000, 
         sw, snw = lattice.saturation()[:2]
         out.append({"pc": float(pc), "rho_in1": float(rin), "S_w": float(sw), "S_nw_smooth": float(snw),
                     "steps": int(steps), "settled": settled})
+    return out
+
+
+def trapped_volume(rho1, rho2, solid, outlet_slices):
+    """Wetting-phase voxels (component 2 the majority, rho2 > rho1) in
+    18-connected clusters that reach neither the outlet reservoir (the last
+    ``outlet_slices`` z slices) nor, through it, the outlet: the volume the
+    displacing phase has cut off."""
+    from scipy import ndimage
+
+    water = (rho2 > rho1) & (solid == 0)
+    lab, n = ndimage.label(water, structure=ndimage.generate_binary_structure(3, 2))
+    if n == 0:
+        return 0
+    tail = lab[-outlet_slices:]
+    connected = np.unique(tail[tail > 0])
+    return int(((lab > 0) & ~np.isin(lab, connected)).sum())
+
+
+def drainage_history(lattice, solid, nsteps, every=500, outlet_slices=8):
+    """Step a drainage ``nsteps`` steps, recording every ``every`` steps the
+    water saturation S_w, the smooth non-wetting saturation and the trapped
+    wetting volume (Section 4.1 outputs).  Returns a list of dicts."""
+    out = []
+    done = 0
+    while done < nsteps:
+        k = min(every, nsteps - done)
+        lattice.step(k)
+        done += k
+        sw, snw = lattice.saturation()[:2]
+        f = lattice.fields(("rho1", "rho2"))
+        out.append({"step": done, "S_w": float(sw), "S_nw_smooth": float(snw),
+                    "trapped": trapped_volume(f["rho1"], f["rho2"], solid, outlet_slices)})
     return out
 
 

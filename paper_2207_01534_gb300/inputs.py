@@ -294,16 +294,18 @@ def drainage_pack_128(seed_offset=1):
 def batched_sweep(count=64, seed_offset=100):
     """Parameter points of the batched sweep: ``count`` independent sphere
     packs, edge n uniform in 48..112, sphere radius uniform in [4, 8], porosity
-    uniform in [0.35, 0.45], viscosity ratio from {1, 5, 10, 50} and contact
-    angle from {30, 60, 90, 120} deg, 6 reservoir slices per end.  Returns one
-    dict per sample; ``batched_sample`` builds its geometry and initial state."""
+    uniform in [0.35, 0.45], 6 reservoir slices per end; sample k takes the
+    (viscosity ratio, contact angle) combination k mod 16 of {1, 5, 10, 50} x
+    {30, 60, 90, 120} deg (so 64 samples are 4 seeds of every combination).
+    Returns one dict per sample; ``batched_sample`` builds its geometry and
+    initial state."""
     rng = np.random.Generator(np.random.PCG64(SEED_BASE + seed_offset))
+    ms, thetas = (1.0, 5.0, 10.0, 50.0), (30.0, 60.0, 90.0, 120.0)
     out = []
     for k in range(count):
         out.append({"n": int(rng.integers(48, 113)), "radius": float(rng.uniform(4.0, 8.0)),
-                    "porosity": float(rng.uniform(0.35, 0.45)), "M": float(rng.choice([1.0, 5.0, 10.0, 50.0])),
-                    "theta_deg": float(rng.choice([30.0, 60.0, 90.0, 120.0])), "reservoir": 6,
-                    "seed": SEED_BASE + seed_offset + 1 + k})
+                    "porosity": float(rng.uniform(0.35, 0.45)), "M": ms[k % 4], "theta_deg": thetas[(k // 4) % 4],
+                    "reservoir": 6, "seed": SEED_BASE + seed_offset + 1 + k})
     return out
 
 

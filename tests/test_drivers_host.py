@@ -40,3 +40,24 @@ def test_lateral_walls():
     assert not w[:, 1:-1, 1:-1].any()
     wx = inputs.add_lateral_walls(s, axes=(0,))
     assert wx[:, :, 0].all() and not wx[:, 1:-1, 1:-1].any() and not wx[:, 0, 1:-1].any()
+
+
+def test_trapped_volume_counts_only_cut_off_water():
+    nz, ny, nx = 12, 6, 6
+    solid = np.zeros((nz, ny, nx), np.uint8)
+    rho1 = np.full(solid.shape, 1.0)  # oil everywhere
+    rho2 = np.full(solid.shape, 0.03)
+    rho2[-3:] = 1.0  # water in the outlet reservoir: connected, not trapped
+    rho1[-3:] = 0.03
+    rho2[2:4, 1:3, 1:3] = 1.0  # a cut-off water blob of 8 voxels
+    rho1[2:4, 1:3, 1:3] = 0.03
+    rho2[6, 4, 4] = 1.0  # a single voxel with no water among its 18 neighbours
+    rho1[6, 4, 4] = 0.03
+    assert drivers.trapped_volume(rho1, rho2, solid, 3) == 9
+    # a water path to the reservoir makes the blob connected
+    rho2[4:9, 2, 2] = 1.0
+    rho1[4:9, 2, 2] = 0.03
+    assert drivers.trapped_volume(rho1, rho2, solid, 3) == 1
+    # solid voxels never count
+    solid[2:4, 1:3, 1:3] = 1
+    assert drivers.trapped_volume(rho1, rho2, solid, 3) == 1

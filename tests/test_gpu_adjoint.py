@@ -168,3 +168,34 @@ def test_autograd_function(lbm):
     assert abs(J.item() - J2) < 1e-12
     assert np.allclose(x.grad.cpu().numpy(), 3.0 * gx, rtol=1e-6, atol=0)
     assert abs(rin.grad.item() - 3.0 * grin) <= 1e-9 * abs(grin)
+
+
+@pytest.mark.parametrize("storage,tol_xi", [("fp32", 1e-4), ("fp64", 2e-7)])
+def test_adjoint_on_the_crop_of_the_96_pack(lbm, storage, tol_xi):
+    """The oracle-adjoint check of the adjoint configuration: the 16^3 crop
+    [0, 16)^3 of the 96^3 pack with 2-slice reservoirs, imbibition start,
+    60 steps, checkpoints every 25."""
+    import torch
+
+    solid = inputs.crop(inputs.adjoint_pack_96()[0], 16, reservoir=2, origin=(0, 0, 0))
+    r1, r2 = inputs.imbibition_init(solid, 2)
+    rng = np.random.default_rng(16)
+    xi = np.where(solid == 1, rng.uniform(-0.4, 0.4, solid.shape), 0.0).astype(np.float32)
+    kw = dict(tau=inputs.tau_for_viscosity_ratio(10.0), G=3.5, periodic=(1, 1, 0), open_axis=2, rho_in1=1.02,
+              rho_out2=1.0)
+    o = oracle.Oracle(solid, xi_field=xi.astype(np.float64), **kw)
+    o.init_densities(r1, r2)
+    o.record(60)
+    go = o.adjoint(2, 14)
+    g = lbm.Lattice(solid, storage=storage, kernel="split", sample=(2, 14), **kw)
+    g.set_xi_field(xi)
+    g.init_densities(r1, r2)
+    g.record(60, 25)
+    gx = torch.zeros(solid.shape, dtype=torch.float32, device="cuda")
+    J, grin = g.adjoint(1.0, gx)
+    gx = gx.cpu().numpy().astype(np.float64)
+    scale = np.abs(go["xi"]).max()
+    err = np.abs(gx - go["xi"]).max() / scale
+    print("%s crop: grad_xi rel L-inf %.2e  grad_rho_in %.6e vs %.6e" % (storage, err, grin, go["rho_in1"]))
+    assert scale > 1e-8 and err <= tol_xi
+    assert abs(grin - go["rho_in1"]) <= 1e-4 * abs(go["rho_in1"]) + 1e-12

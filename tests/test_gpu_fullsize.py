@@ -46,6 +46,19 @@ def test_drainage_pack_128_one_step_against_the_oracle(lbm):
     assert np.abs(a1 - b1).max() <= 2e-6 and np.abs(a2 - b2).max() <= 2e-6
 
 
+def test_drainage_pack_128_history(lbm):
+    """The drainage outputs of the 128^3 configuration every 500 steps (S_w,
+    smooth S_nw, trapped wetting volume): oil enters, S_w falls."""
+    solid, r1, r2, kw, cfg = bench.workload_setup()
+    g = lbm.Lattice(solid, sample=(8, 120), **kw)
+    g.init_densities(r1, r2)
+    h = drivers.drainage_history(g, solid, 1500, every=500, outlet_slices=8)
+    print([(e["step"], round(e["S_w"], 4), e["trapped"]) for e in h])
+    sw = [e["S_w"] for e in h]
+    assert sw[0] < 1.0 and all(b <= a + 1e-3 for a, b in zip(sw, sw[1:])) and sw[-1] < sw[0]
+    assert all(e["trapped"] >= 0 for e in h)
+
+
 @pytest.fixture(scope="module")
 def rock256():
     return inputs.rock_grf_256()
@@ -58,21 +71,28 @@ def _rock_kw():
 
 def test_rock_256_sixteen_bit_against_fp32(lbm, rock256):
     """256^3 random-field rock (porosity 0.22): FP16 / BF16 deviation storage
-    against the FP32 path after 400 steps (saturations of the sample slab)."""
+    against the FP32 path through a drainage (P_c = 0.04, 600 steps) and then
+    an imbibition (the inlet pressure dropped to P_c = -0.02, 600 steps):
+    saturations of the sample slab after each phase."""
     solid, r1, r2 = rock256
-    kw = dict(_rock_kw(), sample=(8, 248))
+    kw = dict(_rock_kw(), sample=(8, 248), rho_in1=drivers.inlet_density(0.04))
     out = {}
     for storage in ("fp32", "fp16dev", "bf16dev"):
         g = lbm.Lattice(solid, storage=storage, **kw)
         g.init_densities(r1, r2)
-        g.step(400)
-        out[storage] = g.saturation()
+        g.step(600)
+        a = g.saturation()
+        g.set_inlet(drivers.inlet_density(-0.02))
+        g.step(600)
+        out[storage] = (a, g.saturation())
         g.close()
-    print({k: tuple(round(x, 5) for x in v[:2]) for k, v in out.items()})
-    assert out["fp32"][0] < 0.999  # the front has entered the sample
+    print({k: [tuple(round(x, 5) for x in v[:2]) for v in p] for k, p in out.items()})
+    (d32, i32) = out["fp32"]
+    assert d32[0] < 0.999 and i32[0] > d32[0]  # oil entered, then water came back
     for storage, bound in (("fp16dev", 0.002), ("bf16dev", 0.01)):
-        assert abs(out[storage][0] - out["fp32"][0]) <= bound
-        assert abs(out[storage][1] - out["fp32"][1]) <= bound
+        for phase in (0, 1):
+            assert abs(out[storage][phase][0] - out["fp32"][phase][0]) <= bound
+            assert abs(out[storage][phase][1] - out["fp32"][phase][1]) <= bound
 
 
 def test_rock_256_crop_against_the_oracle(lbm, rock256):
@@ -100,8 +120,9 @@ def test_rock_256_crop_against_the_oracle(lbm, rock256):
 
 def test_adjoint_pack_96_directional_derivative(lbm):
     """The 96^3 adjoint configuration (500 steps, checkpoints every 50, FP32):
-    the gradient along a random direction of (xi field, inlet density) against
-    a central difference of the FP64 forward (eps = 1e-3)."""
+    the gradient along three random directions of the xi field and along the
+    inlet density against central differences of the FP64 forward
+    (eps = 1e-3)."""
     import torch
 
     solid, r1, r2 = inputs.adjoint_pack_96()
@@ -114,23 +135,26 @@ def test_adjoint_pack_96_directional_derivative(lbm):
     g.record(500, 50)
     gx = torch.zeros(solid.shape, dtype=torch.float32, device="cuda")
     J, grin = g.adjoint(1.0, gx)
+    g64 = gx.cpu().numpy().astype(np.float64)
     rng = np.random.default_rng(96)
-    dx = (rng.standard_normal(solid.shape) * (solid == 1)).astype(np.float32)
-    drin = 0.5
-    pred = float((gx.cpu().numpy().astype(np.float64) * dx).sum()) + grin * drin
+    eps = 1e-3
 
-    def J_at(t):
+    def J_at(dxi, drin, t):
         h = lbm.Lattice(solid, storage="fp64", **dict(kw, rho_in1=kw["rho_in1"] + t * drin))
-        h.set_xi_field((xi + t * dx).astype(np.float32))
+        h.set_xi_field((xi + t * dxi).astype(np.float32))
         h.init_densities(r1, r2)
         h.step(500)
         return h.saturation()[1]
 
-    eps = 1e-3
-    fd = (J_at(eps) - J_at(-eps)) / (2 * eps)
-    print("J %.6f  directional: adjoint %.6e  central difference %.6e" % (J, pred, fd))
-    assert abs(fd) > 1e-7
-    assert abs(pred - fd) <= 1e-2 * abs(fd)
+    zero = np.zeros_like(xi)
+    directions = [(rng.standard_normal(solid.shape).astype(np.float32) * (solid == 1), 0.0) for _ in range(3)]
+    directions.append((zero, 1.0))  # the inlet density alone
+    for dxi, drin in directions:
+        pred = float((g64 * dxi).sum()) + grin * drin
+        fd = (J_at(dxi, drin, eps) - J_at(dxi, drin, -eps)) / (2 * eps)
+        print("J %.6f  directional: adjoint %.6e  central difference %.6e" % (J, pred, fd))
+        assert abs(fd) > 1e-8
+        assert abs(pred - fd) <= 1e-2 * abs(fd)
 
 
 def test_batched_sweep_64_members_equal_their_solo_runs(lbm):

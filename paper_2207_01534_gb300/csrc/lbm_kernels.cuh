@@ -136,11 +136,9 @@ struct Traits<float> {
     using R2 = float2;
     static constexpr bool kDev = false;
     __device__ static __forceinline__ C2 load(const S2 *p, C2) { return __ldg(p); }
-    __device__ static __forceinline__ C2 load_cg(const S2 *p, C2) { return __ldcg(p); }
     __device__ static __forceinline__ void store(S2 *p, C2 v, C2) { *p = v; }
     __device__ static __forceinline__ void store1(S2 *p, int sg, C v, C) { (sg ? p->y : p->x) = v; }
     __device__ static __forceinline__ S2 quant(C2 v, C2) { return v; }
-    __device__ static __forceinline__ C2 dequant(S2 q, C2) { return q; }
     __device__ static __forceinline__ void store_q(S2 *p, S2 q) { *p = q; }
     template <int LD>
     __device__ static __forceinline__ C2 load_dev(const S2 *p) { return ldm<LD>(p); }
@@ -155,11 +153,9 @@ struct Traits<double> {
     using R2 = double2;
     static constexpr bool kDev = false;
     __device__ static __forceinline__ C2 load(const S2 *p, C2) { return __ldg(p); }
-    __device__ static __forceinline__ C2 load_cg(const S2 *p, C2) { return __ldcg(p); }
     __device__ static __forceinline__ void store(S2 *p, C2 v, C2) { *p = v; }
     __device__ static __forceinline__ void store1(S2 *p, int sg, C v, C) { (sg ? p->y : p->x) = v; }
     __device__ static __forceinline__ S2 quant(C2 v, C2) { return v; }
-    __device__ static __forceinline__ C2 dequant(S2 q, C2) { return q; }
     __device__ static __forceinline__ void store_q(S2 *p, S2 q) { *p = q; }
     template <int LD>
     __device__ static __forceinline__ C2 load_dev(const S2 *p) { return ldm<LD>(p); }
@@ -194,17 +190,9 @@ struct Traits16 {
         from_float2(sub2(v, ref), &h);  // one packed, explicitly rounded subtraction
         return h;
     }
-    __device__ static __forceinline__ C2 dequant(S2 q, C2 ref)
-    {
-        return add2(ref, to_float2(q));
-    }
     __device__ static __forceinline__ C2 load(const S2 *p, C2 ref)
     {
         return add2(ref, unpack(__ldg(reinterpret_cast<const unsigned *>(p))));
-    }
-    __device__ static __forceinline__ C2 load_cg(const S2 *p, C2 ref)
-    {
-        return add2(ref, unpack(__ldcg(reinterpret_cast<const unsigned *>(p))));
     }
     __device__ static __forceinline__ void store(S2 *p, C2 v, C2 ref) { *p = quant(v, ref); }
     __device__ static __forceinline__ void store_q(S2 *p, S2 q) { *p = q; }

@@ -81,6 +81,8 @@ __global__ void k_adj_seed(DevState s, AdjState a, double inv_count)
 template <typename TS, int PN>
 __global__ void __launch_bounds__(64) k_adj_plane(DevState sn, AdjState a, int planes)
 {
+    pdl_trigger();
+    pdl_wait();
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
     int p = blockIdx.x * blockDim.x + threadIdx.x;
@@ -208,6 +210,8 @@ struct AdjOcc<double> {
 template <typename TS, int P>
 __global__ void __launch_bounds__(256, AdjOcc<TS>::blocks) k_adj_node(DevState st, AdjState a)
 {
+    pdl_trigger();
+    pdl_wait();
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
     using S2 = typename Traits<TS>::S2;
@@ -353,6 +357,8 @@ __global__ void __launch_bounds__(256, AdjOcc<TS>::blocks) k_adj_node(DevState s
 template <typename TS>
 __global__ void __launch_bounds__(256) k_adj_wall(DevState st, AdjState a)
 {
+    pdl_trigger();
+    pdl_wait();
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
     const int w = blockIdx.x * blockDim.x + threadIdx.x;
@@ -382,6 +388,8 @@ __global__ void __launch_bounds__(256) k_adj_wall(DevState st, AdjState a)
 template <typename TS>
 __global__ void __launch_bounds__(256) k_adj_dens(DevState st, AdjState a)
 {
+    pdl_trigger();
+    pdl_wait();
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -416,6 +424,8 @@ __global__ void __launch_bounds__(256) k_adj_dens(DevState st, AdjState a)
 template <typename TS, int P>
 __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused_to(DevState st, void *f_out, void *rest_out)
 {
+    pdl_trigger();
+    pdl_wait();
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
     const int n = blockIdx.x * blockDim.x + threadIdx.x;
@@ -463,8 +473,8 @@ void Adj<TS>::fused_to(const DevState &s, int parity, void *f_out, void *rest_ou
 {
     if (s.n_fluid == 0) return;
     const int g = (s.n_fluid + 255) / 256;
-    if (parity) k_fused_to<TS, 1><<<g, 256, 0, st>>>(s, f_out, rest_out);
-    else k_fused_to<TS, 0><<<g, 256, 0, st>>>(s, f_out, rest_out);
+    if (parity) launch_pdl(k_fused_to<TS, 1>, (unsigned)g, 256, 0, st, s, f_out, rest_out);
+    else launch_pdl(k_fused_to<TS, 0>, (unsigned)g, 256, 0, st, s, f_out, rest_out);
 }
 
 template <typename TS>
@@ -477,8 +487,8 @@ void Adj<TS>::plane(const DevState &sn, const AdjState &a, int parity_next, int 
 {
     if (!sn.open_z || sn.nxy == 0) return;
     const int g = ((plane == 2 ? 2 : 1) * sn.nxy + 63) / 64;
-    if (parity_next) k_adj_plane<TS, 1><<<g, 64, 0, st>>>(sn, a, plane);
-    else k_adj_plane<TS, 0><<<g, 64, 0, st>>>(sn, a, plane);
+    if (parity_next) launch_pdl(k_adj_plane<TS, 1>, (unsigned)g, 64, 0, st, sn, a, plane);
+    else launch_pdl(k_adj_plane<TS, 0>, (unsigned)g, 64, 0, st, sn, a, plane);
 }
 template <typename TS>
 void Adj<TS>::node(const DevState &s, const AdjState &a, int parity, cudaStream_t st)
@@ -493,18 +503,18 @@ void Adj<TS>::node(const DevState &s, const AdjState &a, int parity, cudaStream_
         attr = true;
     }
     const int g = (s.n_fluid + 255) / 256;
-    if (parity) k_adj_node<TS, 1><<<g, 256, smem, st>>>(s, a);
-    else k_adj_node<TS, 0><<<g, 256, smem, st>>>(s, a);
+    if (parity) launch_pdl(k_adj_node<TS, 1>, (unsigned)g, 256, smem, st, s, a);
+    else launch_pdl(k_adj_node<TS, 0>, (unsigned)g, 256, smem, st, s, a);
 }
 template <typename TS>
 void Adj<TS>::wall(const DevState &s, const AdjState &a, cudaStream_t st)
 {
-    if (s.n_wall > 0) k_adj_wall<TS><<<(s.n_wall + 255) / 256, 256, 0, st>>>(s, a);
+    if (s.n_wall > 0) launch_pdl(k_adj_wall<TS>, (unsigned)((s.n_wall + 255) / 256), 256, 0, st, s, a);
 }
 template <typename TS>
 void Adj<TS>::dens(const DevState &s, const AdjState &a, cudaStream_t st)
 {
-    if (s.n_fluid > 0) k_adj_dens<TS><<<(s.n_fluid + 255) / 256, 256, 0, st>>>(s, a);
+    if (s.n_fluid > 0) launch_pdl(k_adj_dens<TS>, (unsigned)((s.n_fluid + 255) / 256), 256, 0, st, s, a);
 }
 template <typename TS>
 void Adj<TS>::xi_out(const DevState &s, const AdjState &a, double scale, float *grad, cudaStream_t st)

@@ -29,6 +29,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cstdlib>
+
 #include "lbm_internal.h"
 
 namespace lbm {
@@ -271,6 +273,27 @@ __device__ __forceinline__ typename Traits<TS>::C2 density_of(typename Traits<TS
 // blocks are running.  Both are no-ops for an ordinary launch.
 __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" :::); }
+
+// Host side: launch with programmatic stream serialization (the kernel waits
+// for its predecessor itself); the environment variable LBM_NO_PDL turns it
+// off.
+template <typename... KArgs, typename... Args>
+static void launch_pdl(void (*kernel)(KArgs...), unsigned grid, int block, size_t smem, cudaStream_t st,
+                       Args... args)
+{
+    static const bool off = std::getenv("LBM_NO_PDL") != nullptr;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = off ? 0 : 1;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 
 // ---------------------------------------------------------------------------
 // Geometry helpers
@@ -801,6 +824,8 @@ __device__ __forceinline__ const DevState &stage_state(const DevState *states, i
 template <typename TS, int P>
 __global__ void __launch_bounds__(256) k_dens_batch(const DevState *states, const int2 *map, int neem)
 {
+    pdl_trigger();
+    pdl_wait();
     __shared__ __align__(16) DevState sh;
     const int2 m = map[blockIdx.x];
     const DevState &s = stage_state(states, m.x, &sh);
@@ -810,6 +835,8 @@ __global__ void __launch_bounds__(256) k_dens_batch(const DevState *states, cons
 template <typename TS>
 __global__ void __launch_bounds__(256) k_wall_batch(const DevState *states, const int2 *map)
 {
+    pdl_trigger();
+    pdl_wait();
     __shared__ __align__(16) DevState sh;
     const int2 m = map[blockIdx.x];
     const DevState &s = stage_state(states, m.x, &sh);
@@ -820,6 +847,8 @@ __global__ void __launch_bounds__(256) k_wall_batch(const DevState *states, cons
 template <typename TS, int P>
 __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused_batch(const DevState *states, const int2 *map)
 {
+    pdl_trigger();
+    pdl_wait();
     __shared__ __align__(16) DevState sh;
     const int2 m = map[blockIdx.x];
     const DevState &s = stage_state(states, m.x, &sh);

@@ -8,25 +8,6 @@ namespace lbm {
 
 static inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-// Launch with programmatic stream serialization (the kernel waits for its
-// predecessor itself, see pdl_wait); LBM_NO_PDL turns it off.
-template <typename... KArgs, typename... Args>
-static void launch_pdl(void (*kernel)(KArgs...), unsigned grid, int block, cudaStream_t st, Args... args)
-{
-    static const bool off = std::getenv("LBM_NO_PDL") != nullptr;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3((unsigned)block);
-    cfg.dynamicSmemBytes = 0;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = off ? 0 : 1;
-    cudaLaunchKernelEx(&cfg, kernel, args...);
-}
-
 template <typename TS>
 void Ops<TS>::dens(const DevState &s, int parity, int neem, cudaStream_t st, int block, int n0, int n1)
 {
@@ -34,8 +15,8 @@ void Ops<TS>::dens(const DevState &s, int parity, int neem, cudaStream_t st, int
     if (n1 <= n0) return;
     const unsigned g = grid_for(n1 - n0, block);
     const int ne = neem && s.open_z;
-    if (parity) launch_pdl(k_dens<TS, 1>, g, block, st, s, ne, n0, n1);
-    else launch_pdl(k_dens<TS, 0>, g, block, st, s, ne, n0, n1);
+    if (parity) launch_pdl(k_dens<TS, 1>, g, block, 0, st, s, ne, n0, n1);
+    else launch_pdl(k_dens<TS, 0>, g, block, 0, st, s, ne, n0, n1);
 }
 
 template <typename TS>
@@ -43,7 +24,7 @@ void Ops<TS>::wall(const DevState &s, cudaStream_t st, int block, int w0, int w1
 {
     if (w1 < 0) w1 = s.n_wall;
     if (w1 <= w0) return;
-    launch_pdl(k_wall<TS>, grid_for(w1 - w0, block), block, st, s, w0, w1);
+    launch_pdl(k_wall<TS>, grid_for(w1 - w0, block), block, 0, st, s, w0, w1);
 }
 
 template <typename TS>
@@ -52,8 +33,8 @@ void Ops<TS>::fused(const DevState &s, int parity, cudaStream_t st, int block, i
     if (n1 < 0) n1 = s.n_fluid;
     if (n1 <= n0) return;
     const unsigned g = grid_for(n1 - n0, block);
-    if (parity) launch_pdl(k_fused<TS, 1>, g, block, st, s, n0, n1);
-    else launch_pdl(k_fused<TS, 0>, g, block, st, s, n0, n1);
+    if (parity) launch_pdl(k_fused<TS, 1>, g, block, 0, st, s, n0, n1);
+    else launch_pdl(k_fused<TS, 0>, g, block, 0, st, s, n0, n1);
 }
 
 template <typename TS>
@@ -61,23 +42,23 @@ void Ops<TS>::dens_batch(const DevState *states, const int2 *map, int nblocks, i
                          int block)
 {
     if (nblocks <= 0) return;
-    if (parity) k_dens_batch<TS, 1><<<nblocks, block, 0, st>>>(states, map, neem);
-    else k_dens_batch<TS, 0><<<nblocks, block, 0, st>>>(states, map, neem);
+    if (parity) launch_pdl(k_dens_batch<TS, 1>, (unsigned)nblocks, block, 0, st, states, map, neem);
+    else launch_pdl(k_dens_batch<TS, 0>, (unsigned)nblocks, block, 0, st, states, map, neem);
 }
 
 template <typename TS>
 void Ops<TS>::wall_batch(const DevState *states, const int2 *map, int nblocks, cudaStream_t st, int block)
 {
     if (nblocks <= 0) return;
-    k_wall_batch<TS><<<nblocks, block, 0, st>>>(states, map);
+    launch_pdl(k_wall_batch<TS>, (unsigned)nblocks, block, 0, st, states, map);
 }
 
 template <typename TS>
 void Ops<TS>::fused_batch(const DevState *states, const int2 *map, int nblocks, int parity, cudaStream_t st, int block)
 {
     if (nblocks <= 0) return;
-    if (parity) k_fused_batch<TS, 1><<<nblocks, block, 0, st>>>(states, map);
-    else k_fused_batch<TS, 0><<<nblocks, block, 0, st>>>(states, map);
+    if (parity) launch_pdl(k_fused_batch<TS, 1>, (unsigned)nblocks, block, 0, st, states, map);
+    else launch_pdl(k_fused_batch<TS, 0>, (unsigned)nblocks, block, 0, st, states, map);
 }
 
 template <typename TS>

@@ -167,3 +167,33 @@ def test_square_duct_poiseuille():
     uz = o.fields()["uz"][0, 1:-1, 1:-1]
     ref = physics.duct_series_velocity(m, m, g, nu)
     assert np.abs(uz - ref).max() / ref.max() < 0.01
+
+
+def _enclosed_droplet(n=16, r=4.0):
+    """A droplet of component 1 in a closed cubic pore (one-voxel solid shell),
+    surrounded by component 2, viscosity ratio 10, neutral walls."""
+    solid = np.zeros((n, n, n), np.uint8)
+    solid[0] = solid[-1] = 1
+    solid[:, 0] = solid[:, -1] = 1
+    solid[:, :, 0] = solid[:, :, -1] = 1
+    c = (n - 1) / 2.0
+    r1, r2 = inputs.droplet_densities(solid.shape, (c, c, c), r, 2.0, 1.0, 0.03)
+    fl = solid == 0
+    return solid, r1 * fl, r2 * fl
+
+
+def test_enclosed_droplet_keeps_its_volume():
+    """Section 4.1's point that the model preserves trapped volume: a droplet
+    sealed in a closed pore keeps its volume (count of nodes where component 1
+    is the majority) within 1% from step 500 to step 10^4."""
+    solid, r1, r2 = _enclosed_droplet()
+    o = oracle.Oracle(solid, tau=inputs.tau_for_viscosity_ratio(10.0), G=G, periodic=(0, 0, 0))
+    o.init_densities(r1, r2)
+    o.step(500)
+    f = o.fields()
+    v0 = int(((f["rho1"] > f["rho2"]) & (solid == 0)).sum())
+    o.step(9500)
+    f = o.fields()
+    v1 = int(((f["rho1"] > f["rho2"]) & (solid == 0)).sum())
+    assert v0 > 100
+    assert abs(v1 - v0) <= 0.01 * v0, (v0, v1)

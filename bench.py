@@ -78,14 +78,14 @@ def _pc_inlet(G=3.5, minor=0.03, pc=0.02):
     return drivers.inlet_density(pc, G, minor, 1.0)
 
 
-def batch_setup(count=64):
+def batch_setup(count=64, edges=(48, 112)):
     """Geometries of the batched sweep, built in a spawn pool of host processes."""
     import concurrent.futures as cf
     import multiprocessing as mp
 
     from paper_2207_01534_gb300 import inputs
 
-    specs = inputs.batched_sweep(count)
+    specs = inputs.batched_sweep(count, edge_lo=edges[0], edge_hi=edges[1])
     workers = min(len(specs), os.cpu_count() or 1)
     with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
         geo = list(ex.map(inputs.batched_sample, specs))
@@ -96,7 +96,9 @@ def batch_setup(count=64):
                             rho_in1=_pc_inlet(), rho_out2=1.0))
         states.append((r1, r2))
     nf = [int((kw["solid"] == 0).sum()) for kw in samples]
-    cfg = {"workload": BATCH_WORKLOAD, "samples": len(specs), "edges": [sp["n"] for sp in specs],
+    name = BATCH_WORKLOAD if (count, tuple(edges)) == (64, (48, 112)) else "batched_sweep_%d_edges_%d_%d" % (
+        count, edges[0], edges[1])
+    cfg = {"workload": name, "samples": len(specs), "edges": [sp["n"] for sp in specs],
            "n_fluid_total": int(sum(nf)), "n_voxels_total": int(sum(kw["solid"].size for kw in samples)),
            "M": sorted({sp["M"] for sp in specs}), "theta_deg": sorted({sp["theta_deg"] for sp in specs}),
            "Pc": 0.02, "reservoir": 6, "lups_basis": "fluid nodes",
@@ -354,7 +356,7 @@ def run_ours(args, rank, world):
 def run_batch(args, rank, world):
     import tempfile
 
-    samples, states, cfg = batch_setup()
+    samples, states, cfg = batch_setup(args.batch_count, tuple(args.batch_edges))
     import torch
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -523,6 +525,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=(WORKLOAD, BATCH_WORKLOAD, ADJOINT_WORKLOAD))
     ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache (batched workload)")
+    ap.add_argument("--batch-count", type=int, default=64, help="samples (batched workload)")
+    ap.add_argument("--batch-edges", type=int, nargs=2, default=(48, 112), help="edge range (batched workload)")
     ap.add_argument("--adjoint-steps", type=int, default=500, help="recorded steps (adjoint workload)")
     ap.add_argument("--checkpoint-every", type=int, default=50, help="checkpoint interval (adjoint workload)")
     args = ap.parse_args()

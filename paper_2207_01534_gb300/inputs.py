@@ -291,9 +291,10 @@ def drainage_pack_128(seed_offset=1):
     return solid, r1, r2
 
 
-def batched_sweep(count=64, seed_offset=100):
+def batched_sweep(count=64, seed_offset=100, edge_lo=48, edge_hi=112):
     """Parameter points of the batched sweep: ``count`` independent sphere
-    packs, edge n uniform in 48..112, sphere radius uniform in [4, 8], porosity
+    packs, edge n uniform in edge_lo..edge_hi (48..112), sphere radius uniform
+    in [4, 8] (at most n / 6), porosity
     uniform in [0.35, 0.45], 6 reservoir slices per end; sample k takes the
     (viscosity ratio, contact angle) combination k mod 16 of {1, 5, 10, 50} x
     {30, 60, 90, 120} deg (so 64 samples are 4 seeds of every combination).
@@ -303,7 +304,8 @@ def batched_sweep(count=64, seed_offset=100):
     ms, thetas = (1.0, 5.0, 10.0, 50.0), (30.0, 60.0, 90.0, 120.0)
     out = []
     for k in range(count):
-        out.append({"n": int(rng.integers(48, 113)), "radius": float(rng.uniform(4.0, 8.0)),
+        n = int(rng.integers(edge_lo, edge_hi + 1))
+        out.append({"n": n, "radius": min(float(rng.uniform(4.0, 8.0)), n / 6.0),
                     "porosity": float(rng.uniform(0.35, 0.45)), "M": ms[k % 4], "theta_deg": thetas[(k // 4) % 4],
                     "reservoir": 6, "seed": SEED_BASE + seed_offset + 1 + k})
     return out

@@ -302,7 +302,9 @@ def run_ours(args, rank, world):
     achieved = algo * nf / (fused_ms / 1e3) / 1e9
     step_bytes_rate = algo * nf / (ms / args.steps / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": measured_traffic("k_fused"), "kernel": "k_fused", "peak_kind": peak_kind,
+            "traffic": measured_traffic("k_fused") if args.kernel in ("auto", "split") else None,
+            "kernel": {"brick": "k_brick", "push": "k_fused_push", "fused": "k_pipe"}.get(args.kernel, "k_fused"),
+            "peak_kind": peak_kind,
             "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
             "algorithmic_bytes_per_node": algo, "kernel_ms": {names[k]: float(kms[k]) for k in range(5)},
             "step_frac": step_bytes_rate / peak}
@@ -519,7 +521,7 @@ def main():
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--kernel", default="auto", choices=("auto", "split", "fused", "wave", "push"))
+    ap.add_argument("--kernel", default="auto", choices=("auto", "split", "fused", "wave", "push", "brick"))
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp64", "fp16dev", "bf16dev"))
     ap.add_argument("--cpu-steps", type=int, default=20)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -59,7 +59,8 @@ enum {
     LBM_KERNEL_SPLIT = 1, /* density, wall and fused collide-stream passes */
     LBM_KERNEL_FUSED = 2, /* single persistent pass per step (see lbm_step) */
     LBM_KERNEL_WAVE = 3,  /* the split passes per z slab, as a dependency graph (see lbm_step) */
-    LBM_KERNEL_PUSH = 4   /* collide-stream pass that also accumulates the next densities (FP32; see lbm_step) */
+    LBM_KERNEL_PUSH = 4,  /* collide-stream pass that also accumulates the next densities (FP32; see lbm_step) */
+    LBM_KERNEL_BRICK = 5  /* one pass per step over 8^3 bricks, halo densities in shared memory (see lbm_step) */
 };
 
 /* Open-plane rule for the prescribed component (Section 2, boundary rule 1):
@@ -248,7 +249,22 @@ lbm_status lbm_batch_get(lbm_ctx *batch, int32_t k, lbm_ctx **sample);
  * atomic adds and the results are bitwise reproducible); a plane pass then
  * applies the open-plane rule and sets the plane nodes' densities, and the
  * wall pass follows.  The force stencil reads these densities, which differ
- * from FP32 sums by at most a few units of 2^-26.  Graphs replay six steps. */
+ * from FP32 sums by at most a few units of 2^-26.  Graphs replay six steps.
+ *
+ * LBM_KERNEL_BRICK (FP32, FP16 and BF16 storage, single lattices): one launch
+ * per step.  Fluid nodes are numbered brick by brick (8^3 voxels); one block
+ * per brick stages the densities of the brick and a two-voxel halo in shared
+ * memory, computes the virtual densities of the walls of the brick and a
+ * one-voxel halo there (Eq. 15), collides and streams the brick's nodes with
+ * the force stencil read from shared memory, and adds every stored
+ * post-collision population into a shared-memory fixed-point accumulator of
+ * the node it streams into (same encoding as LBM_KERNEL_PUSH).  Cells inside
+ * the brick are then stored and the brick's faces and halo added atomically
+ * into the next step's densities; a plane pass applies the open-plane rule.
+ * No density or wall pass re-reads the populations.  Results agree with the
+ * split schedule to the fixed-point rounding of the densities and are bitwise
+ * reproducible; graphs replay six steps.  lbm_record steps with this
+ * schedule; the reverse pass recomputes its segments with the split passes. */
 
 /* Autotuner: times a few steps of the context's own lattice (or batch) at
  * each candidate block size of the split schedule (64, 128, 256 threads),

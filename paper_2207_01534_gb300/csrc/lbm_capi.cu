@@ -9,6 +9,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "lbm.h"
@@ -63,6 +64,11 @@ struct lbm_ctx {
     unsigned long long *acc[3] = {nullptr, nullptr, nullptr};
     uint32_t *d_nmask = nullptr;
     int64_t push_step = -1;
+    // brick schedule: per-brick tables (lbm_brick.cuh) and the wall ids of
+    // its wall entries (for new coefficients after a change of xi)
+    BrickBufs bb{};
+    int n_bricks = 0, n_bentries = 0;
+    int32_t *d_bwid = nullptr;
     double mass0[2] = {0, 0};
     cudaEvent_t ev[kNumTimed + 1];
     bool have_ev = false;
@@ -306,15 +312,21 @@ lbm_status capture_initial_mass(lbm_ctx *c)
     return LBM_OK;
 }
 
-// Push schedule: the accumulator of the current step from a density and wall
-// pass (any state), and a cleared accumulator for the next step.
+bool acc_schedule(const lbm_ctx *c) { return c->kernel == LBM_KERNEL_PUSH || c->kernel == LBM_KERNEL_BRICK; }
+
+// Push and brick schedules: the accumulator of the current step from a
+// density and wall pass (any state), and a cleared accumulator for the next
+// step.  The brick schedule keeps fluid voxels only (it recomputes walls).
 void push_prime_ctx(lbm_ctx *c)
 {
     if (c->push_step == c->step) return;
     const int par = (int)(c->step & 1);
-    Ops<float>::dens(c->s, par, c->step > 0, c->stream, c->block);
-    Ops<float>::wall(c->s, c->stream, c->block);
-    push_prime(c->s, c->acc[c->step % 3], c->stream);
+    dispatch(c, [&](auto tag) {
+        using TS = decltype(tag);
+        Ops<TS>::dens(c->s, par, c->step > 0, c->stream, c->block);
+        Ops<TS>::wall(c->s, c->stream, c->block);
+    });
+    push_prime(c->s, c->acc[c->step % 3], c->stream, c->kernel != LBM_KERNEL_BRICK);
     cudaMemsetAsync(c->acc[(c->step + 1) % 3], 0, (size_t)c->nv * 8, c->stream);
     c->launches += 3;
     c->push_step = c->step;
@@ -341,6 +353,33 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
         push_wall(c->s, pb.acc, st);
         if (ev) cudaEventRecord(ev[3], st);
         c->launches += 1 + (c->s.open_z ? 1 : 0) + (c->s.n_wall > 0 ? 1 : 0);
+        c->step++;
+        c->push_step = c->step;
+        if (c->p.reduce_every > 0 && c->step % c->p.reduce_every == 0) {
+            run_reduce(c);
+            k_check<<<1, 1, 0, st>>>(c->d_red, c->mass0[0], c->mass0[1], c->p.drift_limit, c->s.open_z ? 0 : 1,
+                                     c->d_flag);
+            c->launches += 1;
+        }
+        return;
+    }
+    if (c->kernel == LBM_KERNEL_BRICK) {
+        push_prime_ctx(c);
+        BrickBufs bb = c->bb;
+        bb.rd = c->acc[c->step % 3];
+        bb.acc = c->acc[(c->step + 1) % 3];
+        bb.clr = c->acc[(c->step + 2) % 3];
+        dispatch(c, [&](auto tag) {
+            using TS = decltype(tag);
+            if constexpr (!std::is_same<TS, double>::value) {
+                if (ev) cudaEventRecord(ev[0], st);
+                brick_step<TS>(c->s, bb, c->n_bricks, par, st);
+                if (ev) cudaEventRecord(ev[1], st);
+                brick_plane<TS>(c->s, bb.acc, 1 - par, st);
+                if (ev) cudaEventRecord(ev[2], st);
+            }
+        });
+        c->launches += (c->n_bricks > 0 ? 1 : 0) + (c->s.open_z ? 1 : 0);
         c->step++;
         c->push_step = c->step;
         if (c->p.reduce_every > 0 && c->step % c->p.reduce_every == 0) {
@@ -523,7 +562,7 @@ lbm_status ensure_graph(lbm_ctx *c)
         c->slab_z = plan_slabs(c);
         if (!c->slab_z.empty()) return capture_wave(c);
     }
-    c->graph_steps = c->kernel == LBM_KERNEL_PUSH ? 6 : 2;
+    c->graph_steps = acc_schedule(c) ? 6 : 2;
     const cudaStream_t user = c->stream;
     const int64_t step0 = c->step, launches0 = c->launches;
     std::vector<int64_t> sub_steps;
@@ -984,14 +1023,29 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     const uint8_t *solid = g->solid;
 
     // compact fluid index in voxel order (x fastest): streaming partners of a
-    // warp's nodes are then mostly contiguous too
+    // warp's nodes are then mostly contiguous too.  The brick schedule numbers
+    // the nodes brick by brick instead (voxel order inside a brick).
+    const bool brick = p->kernel == LBM_KERNEL_BRICK;
+    const int nbx = (nx + kBrick - 1) / kBrick, nby = (ny + kBrick - 1) / kBrick, nbz = (nz + kBrick - 1) / kBrick;
     std::vector<int32_t> cidx((size_t)nv, -1);
     std::vector<uint32_t> pvox;
-    for (int64_t v = 0; v < nv; ++v)
+    auto add_node = [&](int64_t v) {
         if (!solid[v]) {
             cidx[(size_t)v] = (int32_t)pvox.size();
             pvox.push_back((uint32_t)v);
         }
+    };
+    if (brick) {
+        for (int bz = 0; bz < nbz; ++bz)
+            for (int by = 0; by < nby; ++by)
+                for (int bx = 0; bx < nbx; ++bx)
+                    for (int z = bz * kBrick; z < std::min(nz, (bz + 1) * kBrick); ++z)
+                        for (int y = by * kBrick; y < std::min(ny, (by + 1) * kBrick); ++y)
+                            for (int x = bx * kBrick; x < std::min(nx, (bx + 1) * kBrick); ++x)
+                                add_node(x + (int64_t)nx * (y + (int64_t)ny * z));
+    } else {
+        for (int64_t v = 0; v < nv; ++v) add_node(v);
+    }
     const int64_t N = (int64_t)pvox.size();
     std::vector<uint8_t> nflags((size_t)N, 0);
     auto face_bits = [&](const int c[3]) {
@@ -1068,6 +1122,62 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
             plane_w[(size_t)z] = (int)b;
         }
     }
+    // brick tables: per brick with fluid nodes its node range and the wall
+    // voxels of the brick and its one-voxel halo (one entry per halo-region
+    // cell, so a wall seen twice through a short periodic axis has two)
+    std::vector<BrickInfo> binfo;
+    std::vector<uint16_t> nloc;
+    std::vector<uint32_t> wcell;
+    std::vector<int32_t> bwid;
+    std::vector<float> wcoef;
+    if (brick) {
+        std::vector<int32_t> wid_of((size_t)nv, -1);
+        for (int64_t w = 0; w < NW; ++w) wid_of[(size_t)wpvox[(size_t)w]] = (int32_t)w;
+        nloc.assign((size_t)N, 0);
+        int64_t n = 0;
+        for (int bz = 0; bz < nbz; ++bz)
+            for (int by = 0; by < nby; ++by)
+                for (int bx = 0; bx < nbx; ++bx) {
+                    BrickInfo b{};
+                    b.x0 = bx * kBrick;
+                    b.y0 = by * kBrick;
+                    b.z0 = bz * kBrick;
+                    const int ex = std::min(kBrick, nx - b.x0), ey = std::min(kBrick, ny - b.y0),
+                              ez = std::min(kBrick, nz - b.z0);
+                    b.ext = ex | (ey << 8) | (ez << 16);
+                    b.n0 = (int)n;
+                    for (int lz = 0; lz < ez; ++lz)
+                        for (int ly = 0; ly < ey; ++ly)
+                            for (int lx = 0; lx < ex; ++lx)
+                                if (!solid[(b.x0 + lx) + (int64_t)nx * ((b.y0 + ly) + (int64_t)ny * (b.z0 + lz))])
+                                    nloc[(size_t)n++] = (uint16_t)(lx + kBrick * ly + kBrick * kBrick * lz);
+                    b.n1 = (int)n;
+                    if (b.n1 == b.n0) continue;
+                    b.w0 = (int)wcell.size();
+                    for (int lz = -1; lz <= ez; ++lz)
+                        for (int ly = -1; ly <= ey; ++ly)
+                            for (int lx = -1; lx <= ex; ++lx) {
+                                int g[3] = {b.x0 + lx, b.y0 + ly, b.z0 + lz};
+                                bool in = true;
+                                for (int a = 0; a < 3; ++a)
+                                    if (g[a] < 0 || g[a] >= dims[a]) {
+                                        if (!per[a]) in = false;
+                                        g[a] = ((g[a] % dims[a]) + dims[a]) % dims[a];
+                                    }
+                                if (!in) continue;
+                                const int32_t w = wid_of[(size_t)(g[0] + (int64_t)nx * (g[1] + (int64_t)ny * g[2]))];
+                                if (w < 0) continue;
+                                const uint32_t cell = (uint32_t)((lz + 1) * kR1 * kR1 + (ly + 1) * kR1 + (lx + 1));
+                                wcell.push_back((wmask[(size_t)w] & 0x7fffeu) | (cell << 20));
+                                bwid.push_back(w);
+                                const float inv = (float)winv[(size_t)w], xi = (float)wxi[(size_t)w];
+                                wcoef.push_back((1.f + xi) * inv);
+                                wcoef.push_back((1.f - xi) * inv);
+                            }
+                    b.w1 = (int)wcell.size();
+                    binfo.push_back(b);
+                }
+    }
     if (18 * (((N + 63) / 64) * 64 + 64) >= ((int64_t)1 << 31))
         return fail(nullptr, LBM_ERR_UNSUPPORTED, "more than 113 million fluid nodes in one context");
 
@@ -1087,10 +1197,15 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     c->kernel = p->kernel == LBM_KERNEL_FUSED ? LBM_KERNEL_FUSED
                 : p->kernel == LBM_KERNEL_WAVE    ? LBM_KERNEL_WAVE
                 : p->kernel == LBM_KERNEL_PUSH    ? LBM_KERNEL_PUSH
+                : p->kernel == LBM_KERNEL_BRICK   ? LBM_KERNEL_BRICK
                                                   : LBM_KERNEL_SPLIT;
     if (c->kernel == LBM_KERNEL_PUSH && c->storage != LBM_STORE_FP32) {
         delete c;
         return fail(nullptr, LBM_ERR_UNSUPPORTED, "the push schedule needs FP32 storage");
+    }
+    if (c->kernel == LBM_KERNEL_BRICK && c->storage == LBM_STORE_FP64) {
+        delete c;
+        return fail(nullptr, LBM_ERR_UNSUPPORTED, "the brick schedule needs FP32, FP16 or BF16 storage");
     }
 
     const size_t sz = p->storage == LBM_STORE_FP64 ? 8 : (is16(p->storage) ? 2 : 4);  // stored element bytes
@@ -1154,6 +1269,17 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     c->d_partials = (double *)A((size_t)kReduceBlocks * kReduceSlots * 8);
     c->d_red = (double *)A((size_t)kReduceSlots * 8);
     std::vector<uint32_t> nmask;
+    if (brick) {
+        for (int q = 0; q < 3; ++q) c->acc[q] = (unsigned long long *)A((size_t)nv * 8);
+        c->n_bricks = (int)binfo.size();
+        c->n_bentries = (int)wcell.size();
+        c->bb.info = (const BrickInfo *)A(std::max<size_t>(1, binfo.size()) * sizeof(BrickInfo));
+        c->bb.nloc = (const uint16_t *)A(std::max<size_t>(1, nloc.size()) * 2);
+        c->bb.wcell = (const uint32_t *)A(std::max<size_t>(1, wcell.size()) * 4);
+        c->bb.wcoef = (const float2 *)A(std::max<size_t>(1, wcell.size()) * 8);
+        c->d_bwid = (int32_t *)A(std::max<size_t>(1, bwid.size()) * 4);
+        c->bb.per = per[0] | (per[1] << 1) | (per[2] << 2);
+    }
     if (c->kernel == LBM_KERNEL_PUSH) {
         for (int q = 0; q < 3; ++q) c->acc[q] = (unsigned long long *)A((size_t)nv * 8);
         c->d_nmask = (uint32_t *)A((size_t)N * 4);
@@ -1270,6 +1396,15 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     H2D(d_nflags, nflags.data(), (size_t)N);
     if (c->d_nmask) H2D(c->d_nmask, nmask.data(), (size_t)N * 4);
     H2D(d_cidx, cidx.data(), (size_t)nv * 4);
+    if (brick) {
+        H2D((void *)c->bb.info, binfo.data(), binfo.size() * sizeof(BrickInfo));
+        H2D((void *)c->bb.nloc, nloc.data(), nloc.size() * 2);
+        H2D((void *)c->bb.wcell, wcell.data(), wcell.size() * 4);
+        H2D((void *)c->bb.wcoef, wcoef.data(), wcoef.size() * 4);
+        H2D(c->d_bwid, bwid.data(), bwid.size() * 4);
+        for (int q = 0; q < 3; ++q)
+            if (e == cudaSuccess) e = cudaMemset(c->acc[q], 0, (size_t)nv * 8);
+    }
     H2D(d_wpvox, wpvox.data(), (size_t)NW * 4);
     H2D(d_wmask, wmask.data(), (size_t)NW * 4);
     H2D(d_winv, winv_h, (size_t)NW * szc);
@@ -1433,8 +1568,8 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
         }
     }
     int64_t k = 0;
-    if (c->kernel == LBM_KERNEL_PUSH && n > 0) push_prime_ctx(c);
-    const int align = c->kernel == LBM_KERNEL_PUSH ? 6 : 2;
+    if (acc_schedule(c) && n > 0) push_prime_ctx(c);
+    const int align = acc_schedule(c) ? 6 : 2;
     const bool graphs = c->kernel != LBM_KERNEL_FUSED && !any_reduce(c) && n >= 2 * align &&
                         std::getenv("LBM_NO_GRAPH") == nullptr;
     if (graphs) {
@@ -1449,7 +1584,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
             for (; n - k >= gs; k += gs) {
                 cudaGraphLaunch(c->graph, c->stream);
                 c->step += gs;
-                if (c->kernel == LBM_KERNEL_PUSH) c->push_step = c->step;
+                if (acc_schedule(c)) c->push_step = c->step;
                 for (lbm_ctx *q : c->subs) q->step += gs;
                 c->launches += c->graph_launches;
             }
@@ -1468,7 +1603,7 @@ lbm_status lbm_create_batch(int32_t n, const lbm_geometry *geoms, const lbm_para
     std::vector<lbm_ctx *> subs;
     for (int32_t k = 0; k < n; ++k) {
         lbm_params pk = params[k];
-        if (pk.kernel == LBM_KERNEL_FUSED) pk.kernel = LBM_KERNEL_SPLIT;
+        if (pk.kernel == LBM_KERNEL_FUSED || pk.kernel == LBM_KERNEL_BRICK) pk.kernel = LBM_KERNEL_SPLIT;
         lbm_ctx *q = nullptr;
         lbm_status st = lbm_create(&geoms[k], &pk, &q);
         if (st == LBM_OK && q->storage != (subs.empty() ? q->storage : subs[0]->storage)) {
@@ -1524,9 +1659,20 @@ lbm_status lbm_step_timed(lbm_ctx *c, int64_t n, double *kernel_ms, int32_t nk)
         for (auto &ev : c->ev) cudaEventCreate(&ev);
         c->have_ev = true;
     }
-    if (c->kernel == LBM_KERNEL_PUSH) push_prime_ctx(c);
+    if (acc_schedule(c)) push_prime_ctx(c);
     for (int64_t k = 0; k < n; ++k) {
         enqueue_step(c, c->ev);
+        if (c->kernel == LBM_KERNEL_BRICK) {  // brick launch, plane pass
+            cudaError_t e = cudaEventSynchronize(c->ev[2]);
+            if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_timed");
+            const int slot[2] = {2, 3};
+            for (int q = 0; q < 2; ++q) {
+                float ms = 0;
+                cudaEventElapsedTime(&ms, c->ev[q], c->ev[q + 1]);
+                if (slot[q] < nk) kernel_ms[slot[q]] += ms;
+            }
+            continue;
+        }
         if (c->kernel == LBM_KERNEL_PUSH) {  // collide-stream, plane, wall
             cudaError_t e = cudaEventSynchronize(c->ev[3]);
             if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_timed");
@@ -1717,6 +1863,11 @@ lbm_status lbm_set_xi_field(lbm_ctx *c, const float *xi, int32_t on_device)
         else
             k_set_wxi<float><<<g, 256, 0, c->stream>>>(c->s.wpvox, c->s.n_wall, src, (float *)c->s.wxi);
         c->launches += 1;
+        if (c->kernel == LBM_KERNEL_BRICK && c->n_bentries > 0) {
+            brick_coef(c->s, c->d_bwid, c->n_bentries, const_cast<float2 *>(c->bb.wcoef),
+                       c->storage == LBM_STORE_FP64, c->stream);
+            c->launches += 1;
+        }
     }
     if (tmp) {
         cudaStreamSynchronize(c->stream);

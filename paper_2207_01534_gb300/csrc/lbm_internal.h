@@ -139,7 +139,44 @@ void push_fused(const DevState &s, const PushBufs &pb, int parity, cudaStream_t 
 void push_plane(const DevState &s, unsigned long long *acc, int parity_next, cudaStream_t st);
 void push_wall(const DevState &s, unsigned long long *acc, cudaStream_t st);
 // densities from the float psi of a density + wall pass (fluid and wall voxels)
-void push_prime(const DevState &s, unsigned long long *acc, cudaStream_t st);
+// (walls = false: fluid voxels only, as the brick schedule keeps them)
+void push_prime(const DevState &s, unsigned long long *acc, cudaStream_t st, bool walls = true);
+
+// Brick schedule (all but FP64 storage, lbm_brick.cu): one block per brick
+// of 8^3 voxels collides and streams the brick's nodes, with the densities of
+// the brick and its halo, the virtual densities of its walls and the next
+// step's density accumulators in shared memory.  Fluid nodes are numbered
+// brick by brick.
+constexpr int kBrick = 8;        // brick edge (voxels)
+constexpr int kR1 = kBrick + 2;  // brick plus a one-voxel halo
+constexpr int kR2 = kBrick + 4;  // brick plus a two-voxel halo
+constexpr int kR1Cells = kR1 * kR1 * kR1;
+constexpr int kR2Cells = kR2 * kR2 * kR2;
+constexpr int kBrickThreads = 128;
+constexpr int kBrickBlocks = 768 / kBrickThreads;  // resident blocks per SM (80 registers a thread)
+struct BrickInfo {
+    int x0, y0, z0;  // origin (voxels)
+    int ext;         // extents bx | by << 8 | bz << 16 (clipped at the domain's end)
+    int n0, n1;      // its fluid nodes
+    int w0, w1;      // its wall entries: the walls of the brick and its one-voxel halo
+};
+struct BrickBufs {
+    const BrickInfo *info;          // [bricks with fluid nodes]
+    const uint16_t *nloc;           // [n_fluid] lx + 8 ly + 64 lz inside the node's brick
+    const uint32_t *wcell;          // [entries] fluid-direction mask (bits 1..18) | halo-region cell << 20
+    const float2 *wcoef;            // [entries] ((1 + xi) / W, (1 - xi) / W), W the Eq. 15 denominator
+    const unsigned long long *rd;   // densities of this step (fluid voxels)
+    unsigned long long *acc;        // next step's accumulators (face and halo voxels cleared)
+    unsigned long long *clr;        // the buffer whose face voxels this step clears
+    int per;                        // periodic axes: bit 0 x, bit 1 y, bit 2 z
+};
+template <typename TS>
+void brick_step(const DevState &s, const BrickBufs &bb, int nbricks, int parity, cudaStream_t st);
+// plane nodes after the brick launch: open-plane rule at the next parity, density totals
+template <typename TS>
+void brick_plane(const DevState &s, unsigned long long *acc, int parity_next, cudaStream_t st);
+// wall coefficients of the brick entries from the wall arrays (after a new xi field)
+void brick_coef(const DevState &s, const int32_t *wid, int n, float2 *coef, bool fp64, cudaStream_t st);
 
 constexpr int kReduceBlocks = 1024;
 constexpr int kReduceThreads = 256;

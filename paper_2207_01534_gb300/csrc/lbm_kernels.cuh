@@ -416,8 +416,10 @@ __device__ __forceinline__ void load_pops(typename Traits<TS>::C2 f[19], typenam
 // are quantised first and the rest deviation is dm minus the stored moving
 // deviations, so the stored mass equals the mass before collision exactly up
 // to FP32 rounding of deviation-sized terms; the codes are stored as computed
-// (never re-quantised).
-template <typename TS, int P>
+// (never re-quantised).  kBack: f[] receives the stored values back (the
+// dequantised codes and the stored rest population), as a later load would
+// return them.
+template <typename TS, int P, bool kBack = false>
 __device__ __forceinline__ void store_pops(typename Traits<TS>::C2 f[19], typename Traits<TS>::C2 dm, int n,
                                            uint32_t pv, uint32_t fl, const Nbr &b, const DevState &s)
 {
@@ -433,6 +435,11 @@ __device__ __forceinline__ void store_pops(typename Traits<TS>::C2 f[19], typena
 #pragma unroll
         for (int i = 2; i < 19; ++i) sum = add2(sum, Traits<TS>::code_value(q[i]));
         st_rest_dev<TS>(s, n, sub2(dm, sum));
+        if constexpr (kBack) {
+            f[0] = add2(sub2(dm, sum), ref_of<TS>(s, 0));
+#pragma unroll
+            for (int i = 1; i < 19; ++i) f[i] = add2(Traits<TS>::code_value(q[i]), ref_of<TS>(s, i));
+        }
     } else {
         st_rest_dev<TS>(s, n, f[0]);
     }

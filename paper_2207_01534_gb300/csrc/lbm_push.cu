@@ -25,11 +25,12 @@ void push_wall(const DevState &s, unsigned long long *acc, cudaStream_t st)
     k_wall_push<<<(s.n_wall + 255) / 256, 256, 0, st>>>(s, acc);
 }
 
-void push_prime(const DevState &s, unsigned long long *acc, cudaStream_t st)
+void push_prime(const DevState &s, unsigned long long *acc, cudaStream_t st, bool walls)
 {
-    const long long n = s.nv > s.n_wall ? s.nv : s.n_wall;
+    const int nw = walls ? s.n_wall : 0;
+    const long long n = s.nv > nw ? s.nv : nw;
     k_psi_to_acc<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<const float2 *>(s.psi), s.cidx,
-                                                              s.wpvox, s.n_wall, s.nv, acc);
+                                                              s.wpvox, nw, s.nv, acc);
 }
 
 }  // namespace lbm

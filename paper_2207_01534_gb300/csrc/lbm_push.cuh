@@ -11,15 +11,8 @@
 // incoming populations.  Plane nodes are finished afterwards by the plane
 // pass (the open-plane rule rewrites populations there), then walls (Eq. 15).
 //
-// Accumulators are integer fixed point so that the sums do not depend on the
-// order of the atomic adds (results are bitwise reproducible): one 64-bit
-// word per voxel holds both components, 32 bits each.  A contribution v is
-// encoded as round(v * 2^26) + 2^25, non-negative for v >= -1/2; 19 encoded
-// contributions stay below 2^32 for v < 3/2, so the low half never carries
-// into the high half.  A density is decoded as (sum - 19 * 2^25) / 2^26 and
-// a wall's virtual density (or a plane node's density) is stored as one
-// encoded total with the same offset.  Resolution 2^-26 = 1.5e-8, finer than
-// FP32 at unit density.
+// Accumulators are integer fixed point (lbm_fixed.cuh): the sums do not
+// depend on the order of the atomic adds, so results are bitwise reproducible.
 //
 // Three accumulator buffers rotate: the pass of step t reads buffer t % 3 in
 // its force stencil, adds into (t + 1) % 3, and clears its own voxel of
@@ -27,39 +20,10 @@
 // of step t + 1 adds into.
 #pragma once
 
+#include "lbm_fixed.cuh"
 #include "lbm_kernels.cuh"
 
 namespace lbm {
-
-constexpr int kFixShift = 26;
-constexpr uint32_t kFixBias = 1u << 25;
-constexpr uint32_t kFixOffset = 19u * kFixBias;  // the bias of 19 contributions
-
-__device__ __forceinline__ uint32_t fix_enc(float v)
-{
-    return (uint32_t)__float2int_rn(v * (float)(1 << kFixShift)) + kFixBias;
-}
-
-__device__ __forceinline__ unsigned long long fix_enc2(float2 v)
-{
-    return (unsigned long long)fix_enc(v.x) | ((unsigned long long)fix_enc(v.y) << 32);
-}
-
-// one stored total (plane node density, wall virtual density)
-__device__ __forceinline__ unsigned long long fix_total2(float2 v)
-{
-    const uint32_t a = (uint32_t)__float2int_rn(v.x * (float)(1 << kFixShift)) + kFixOffset;
-    const uint32_t b = (uint32_t)__float2int_rn(v.y * (float)(1 << kFixShift)) + kFixOffset;
-    return (unsigned long long)a | ((unsigned long long)b << 32);
-}
-
-__device__ __forceinline__ float2 fix_dec2(unsigned long long w)
-{
-    const int a = (int)((uint32_t)w - kFixOffset);
-    const int b = (int)((uint32_t)(w >> 32) - kFixOffset);
-    const float k = 1.0f / (float)(1 << kFixShift);
-    return make_float2((float)a * k, (float)b * k);
-}
 
 // Force of Eqs. 10, 11, 13 from the accumulator densities (as forces()).
 __device__ __forceinline__ void forces_acc(float2 rho, uint32_t pv, uint32_t fl, const Nbr &b, const DevState &s,

@@ -21,7 +21,7 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_ALLOC", -3: "LBM_ERR_CUDA
           -5: "LBM_ERR_DRIFT", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_UNSUPPORTED"}
 BC = {"neem": 0, "zou_he": 1}
 STORAGE = {"fp32": 0, "fp64": 1, "fp16dev": 2, "bf16dev": 3}
-KERNEL = {"auto": 0, "split": 1, "fused": 2, "wave": 3, "push": 4}
+KERNEL = {"auto": 0, "split": 1, "fused": 2, "wave": 3, "push": 4, "brick": 5}
 FIELDS = ("rho1", "rho2", "ux", "uy", "uz", "P")
 
 

@@ -158,16 +158,16 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or
-    None when there is none for the current kernel sources."""
+def measured_traffic(kernel, storage):
+    """DRAM bytes per launch of `kernel` with `storage` from the committed ncu
+    summary, or None when there is none for the current kernel sources."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    e = d.get(WORKLOAD, {}).get(kernel)
+    e = d.get(WORKLOAD, {}).get(storage, {}).get(kernel)
     if not e or e.get("source_hash") != kernel_source_hash():
         return None
     return e.get("dram_bytes_per_launch")
@@ -302,7 +302,7 @@ def run_ours(args, rank, world):
     achieved = algo * nf / (fused_ms / 1e3) / 1e9
     step_bytes_rate = algo * nf / (ms / args.steps / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": measured_traffic("k_fused") if args.kernel in ("auto", "split") else None,
+            "traffic": measured_traffic("k_fused", args.storage) if args.kernel in ("auto", "split") else None,
             "kernel": {"brick": "k_brick", "push": "k_fused_push", "fused": "k_pipe"}.get(args.kernel, "k_fused"),
             "peak_kind": peak_kind,
             "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,

@@ -333,7 +333,7 @@ def run_ours(args, rank, world):
 
         v, done, cdt = oracle_rate(solid, r1, r2, kw, steps=args.cpu_steps)
         oracle.set_threads(1)
-        v1, done1, cdt1 = oracle_rate(solid, r1, r2, kw, steps=2, budget_s=15.0)
+        v1, done1, cdt1 = oracle_rate(solid, r1, r2, kw, steps=3, budget_s=15.0)
         oracle.set_threads(os.cpu_count() or 1)
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
                "sample": "%d full steps of the %s workload (%.1f s); one core: %d steps (%.1f s)" % (
@@ -523,7 +523,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--kernel", default="auto", choices=("auto", "split", "fused", "wave", "push", "brick"))
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp64", "fp16dev", "bf16dev"))
-    ap.add_argument("--cpu-steps", type=int, default=20)
+    ap.add_argument("--cpu-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default=WORKLOAD, choices=(WORKLOAD, BATCH_WORKLOAD, ADJOINT_WORKLOAD))
     ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache (batched workload)")

@@ -31,7 +31,7 @@ def test_choose_schedule(lbm, tmp_path, storage):
     kw = dict(tau=(1.7, 0.62), G=3.5, xi=-0.3, periodic=(1, 1, 0), open_axis=2, rho_in1=1.1, rho_out2=1.0,
               storage=storage)
     path, blocks = str(tmp_path / "sched.json"), str(tmp_path / "blocks.json")
-    e = tune.choose_schedule(solid, (r1, r2), steps=8, warmup=2, cache_path=path, block_cache=blocks, **kw)
+    e = tune.choose_schedule(solid, (r1, r2), cache_path=path, block_cache=blocks, **kw)
     print(e)
     assert set(e["timings"]) == set(tune.candidates(storage))
     assert e["kernel"] == min(e["timings"], key=e["timings"].get) and all(v > 0 for v in e["timings"].values())

@@ -149,10 +149,16 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(sm)}
 
 
+# the files that define and instantiate the split passes (k_dens, k_wall,
+# k_fused) whose DRAM traffic profiles/traffic.json records
+TRAFFIC_SOURCES = ("lbm_internal.h", "lbm_kernels.cuh", "lbm_ops.inl", "lbm_fp32.cu", "lbm_fp64.cu", "lbm_fp16.cu",
+                   "lbm_bf16.cu")
+
+
 def kernel_source_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2207_01534_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in TRAFFIC_SOURCES:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

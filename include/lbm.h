@@ -226,10 +226,11 @@ int32_t lbm_batch_size(const lbm_ctx *batch);
 lbm_status lbm_batch_get(lbm_ctx *batch, int32_t k, lbm_ctx **sample);
 
 /* lbm_step on a single lattice or a batch with the split schedule,
- * reduce_every = 0 and n >= 4 replays two steps at a time from a CUDA graph,
- * captured once on a private stream at the first even step after step 0 and
- * recaptured after any change of the lattice's parameters.  Setting the
- * environment variable LBM_NO_GRAPH disables it.
+ * reduce_every = 0 and n >= 4 replays steps from two CUDA graphs, captured
+ * once on a private stream at the first even step after step 0 and
+ * recaptured after any change of the lattice's parameters: 32 steps at a time
+ * while at least 32 remain, then two at a time.  Setting the environment
+ * variable LBM_NO_GRAPH disables them.
  *
  * LBM_KERNEL_WAVE (single lattices): the same three passes, launched per slab
  * of whole z planes (at least two per slab) from a graph of G steps (G = 4, or
@@ -249,7 +250,8 @@ lbm_status lbm_batch_get(lbm_ctx *batch, int32_t k, lbm_ctx **sample);
  * atomic adds and the results are bitwise reproducible); a plane pass then
  * applies the open-plane rule and sets the plane nodes' densities, and the
  * wall pass follows.  The force stencil reads these densities, which differ
- * from FP32 sums by at most a few units of 2^-26.  Graphs replay six steps.
+ * from FP32 sums by at most a few units of 2^-26.  Graphs replay 30 steps
+ * while at least 30 remain, then six.
  *
  * LBM_KERNEL_BRICK (FP32, FP16 and BF16 storage, single lattices): one launch
  * per step.  Fluid nodes are numbered brick by brick (8^3 voxels); one block
@@ -263,7 +265,7 @@ lbm_status lbm_batch_get(lbm_ctx *batch, int32_t k, lbm_ctx **sample);
  * into the next step's densities; a plane pass applies the open-plane rule.
  * No density or wall pass re-reads the populations.  Results agree with the
  * split schedule to the fixed-point rounding of the densities and are bitwise
- * reproducible; graphs replay six steps.  lbm_record steps with this
+ * reproducible; graphs replay as for LBM_KERNEL_PUSH.  lbm_record steps with this
  * schedule; the reverse pass recomputes its segments with the split passes. */
 
 /* Autotuner: times a few steps of the context's own lattice (or batch) at

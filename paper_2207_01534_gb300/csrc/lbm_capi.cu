@@ -87,6 +87,10 @@ struct lbm_ctx {
     cudaGraphExec_t graph = nullptr;
     bool graph_dirty = true;
     int64_t graph_launches = 0;  // kernels per replay
+    // a short graph for the steps left over after the long one's replays
+    cudaGraphExec_t graph_short = nullptr;
+    int64_t graph_short_launches = 0;
+    int graph_short_steps = 0;
     int graph_steps = 2;         // steps per replay
     // wavefront schedule: per-plane prefix counts of fluid nodes and walls,
     // slab boundaries (z planes), and the capture streams / events
@@ -549,20 +553,10 @@ std::vector<int> plan_slabs(const lbm_ctx *c)
 
 lbm_status capture_wave(lbm_ctx *c);
 
-lbm_status ensure_graph(lbm_ctx *c)
+// Capture `steps` steps on the private stream into *out; the step counters
+// and the launch count are put back afterwards (*launches: kernels per replay).
+lbm_status capture_steps(lbm_ctx *c, int steps, cudaGraphExec_t *out, int64_t *launches)
 {
-    if (c->graph && !c->graph_dirty) return LBM_OK;
-    if (c->graph) {
-        cudaGraphExecDestroy(c->graph);
-        c->graph = nullptr;
-    }
-    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
-        return cuda_fail(c, cudaGetLastError(), "graph stream");
-    if (c->kernel == LBM_KERNEL_WAVE && c->subs.empty()) {
-        c->slab_z = plan_slabs(c);
-        if (!c->slab_z.empty()) return capture_wave(c);
-    }
-    c->graph_steps = acc_schedule(c) ? 6 : 2;
     const cudaStream_t user = c->stream;
     const int64_t step0 = c->step, launches0 = c->launches;
     std::vector<int64_t> sub_steps;
@@ -571,21 +565,51 @@ lbm_status ensure_graph(lbm_ctx *c)
     const int64_t push0 = c->push_step;
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess)
-        for (int q = 0; q < c->graph_steps; ++q) step_once(c);
+        for (int q = 0; q < steps; ++q) step_once(c);
     cudaGraph_t g = nullptr;
     cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &g) : e;
     c->stream = user;
     c->step = step0;
     c->push_step = push0;
     for (size_t k = 0; k < c->subs.size(); ++k) c->subs[k]->step = sub_steps[k];
-    c->graph_launches = c->launches - launches0;
+    *launches = c->launches - launches0;
     c->launches = launches0;
-    if (e2 == cudaSuccess) e2 = cudaGraphInstantiate(&c->graph, g, 0);
+    if (e2 == cudaSuccess) e2 = cudaGraphInstantiate(out, g, 0);
     if (g) cudaGraphDestroy(g);
     if (e2 != cudaSuccess) {
-        c->graph = nullptr;
+        *out = nullptr;
         return cuda_fail(c, e2, "graph capture");
     }
+    return LBM_OK;
+}
+
+lbm_status ensure_graph(lbm_ctx *c)
+{
+    if (c->graph && !c->graph_dirty) return LBM_OK;
+    if (c->graph) {
+        cudaGraphExecDestroy(c->graph);
+        c->graph = nullptr;
+    }
+    if (c->graph_short) {
+        cudaGraphExecDestroy(c->graph_short);
+        c->graph_short = nullptr;
+        c->graph_short_steps = 0;
+    }
+    if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return cuda_fail(c, cudaGetLastError(), "graph stream");
+    if (c->kernel == LBM_KERNEL_WAVE && c->subs.empty()) {
+        c->slab_z = plan_slabs(c);
+        if (!c->slab_z.empty()) return capture_wave(c);
+    }
+    // long graph: 32 steps (30 for the accumulator schedules, whose buffers
+    // rotate every three steps and parity every two); short graph: one period
+    const int period = acc_schedule(c) ? 6 : 2;
+    lbm_status st = capture_steps(c, acc_schedule(c) ? 30 : 32, &c->graph, &c->graph_launches);
+    if (st != LBM_OK) return st;
+    c->graph_steps = acc_schedule(c) ? 30 : 32;
+    st = capture_steps(c, period, &c->graph_short, &c->graph_short_launches);
+    if (st != LBM_OK) return st;
+    c->graph_short_steps = period;
     c->graph_dirty = false;
     return LBM_OK;
 }
@@ -726,6 +750,7 @@ void destroy_ctx(lbm_ctx *c)
     else cudaDeviceSynchronize();
     for (lbm_ctx *q : c->subs) destroy_ctx(q);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->graph_short) cudaGraphExecDestroy(c->graph_short);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (cudaStream_t st : c->wave_streams) cudaStreamDestroy(st);
     for (cudaEvent_t ev : c->wave_events) cudaEventDestroy(ev);
@@ -1580,13 +1605,19 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
             ++k;
         }
         if (n - k >= 2 && ensure_graph(c) == LBM_OK) {
-            const int gs = c->graph_steps;
-            for (; n - k >= gs; k += gs) {
-                cudaGraphLaunch(c->graph, c->stream);
-                c->step += gs;
-                if (acc_schedule(c)) c->push_step = c->step;
-                for (lbm_ctx *q : c->subs) q->step += gs;
-                c->launches += c->graph_launches;
+            // the long graph while it fits, then the short one
+            const cudaGraphExec_t gx[2] = {c->graph, c->graph_short};
+            const int gn[2] = {c->graph_steps, c->graph_short_steps};
+            const int64_t gl[2] = {c->graph_launches, c->graph_short_launches};
+            for (int q = 0; q < 2; ++q) {
+                if (!gx[q] || gn[q] <= 0) continue;
+                for (; n - k >= gn[q]; k += gn[q]) {
+                    cudaGraphLaunch(gx[q], c->stream);
+                    c->step += gn[q];
+                    if (acc_schedule(c)) c->push_step = c->step;
+                    for (lbm_ctx *qq : c->subs) qq->step += gn[q];
+                    c->launches += gl[q];
+                }
             }
         }
     }

@@ -207,7 +207,7 @@ def test_bitwise_reproducible_with_and_without_graphs(lbm):
         try:
             g = lbm.Lattice(solid, kernel="brick", **kw)
             g.init_densities(r1, r2)
-            for n in (1, 4, 29, 13):  # off-period starts, replays and a ragged tail
+            for n in (1, 4, 29, 13, 70):  # off-period starts, short and long replays, ragged tails
                 g.step(n)
             out.append(g.get_populations())
         finally:

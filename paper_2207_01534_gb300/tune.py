@@ -14,10 +14,11 @@ The candidates differ in kernel structure and in memory layout:
   different layout), so it needs its own context.
 
 Each candidate gets a fresh lattice with the caller's parameters and initial
-densities, ``warmup`` untimed steps (enough for the CUDA graph to be captured:
-the push and brick schedules replay six steps per graph, the others two),
-then ``steps`` steps timed with CUDA events on the lattice's stream (a
-multiple of six keeps every timed step inside a replay).  The cache is a flat JSON object mapping a
+densities, ``warmup`` untimed steps (enough for its CUDA graphs to be captured
+and replayed once), then ``steps`` steps timed with CUDA events on the
+lattice's stream.  The split and wave schedules replay 32-step graphs (then
+2-step ones), push and brick 30-step graphs (then 6-step ones): the default 96
+timed steps are long-graph replays plus at most one short one.  The cache is a flat JSON object mapping a
 key (GPU name, compute capability, storage, grid shape, periodic axes, open
 axis, fluid count and a hash of the solid mask) to the chosen entry; a cached
 key is returned without creating or timing anything.
@@ -96,7 +97,7 @@ def _event_timer(lat, steps, warmup):
     return e0.elapsed_time(e1) / steps
 
 
-def choose_schedule(solid, rho, steps=24, warmup=16, cache_path=None, block_cache=None, kernels=None, lattice=None,
+def choose_schedule(solid, rho, steps=96, warmup=40, cache_path=None, block_cache=None, kernels=None, lattice=None,
                     timer=None, device=None, **kw):
     """Time the candidate schedules on this lattice and return the fastest as
     {"kernel", "block", "ms_per_step", "timings": {kernel: ms}, "key"}.

@@ -269,7 +269,8 @@ lbm_status lbm_batch_get(lbm_ctx *batch, int32_t k, lbm_ctx **sample);
  * schedule; the reverse pass recomputes its segments with the split passes. */
 
 /* Autotuner: times a few steps of the context's own lattice (or batch) at
- * each candidate block size of the split schedule (64, 128, 256 threads),
+ * each candidate block size of the split schedule (64, 128, 256 threads;
+ * 128 until the autotuner chooses),
  * keeps the fastest, and caches it in the JSON file cache_path (a flat object
  * of "key": block pairs; the key names the GPU, compute capability, storage
  * type, batch size and node counts).  A cached key is applied without timing.

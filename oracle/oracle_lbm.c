@@ -16,7 +16,7 @@
  *   - neighbour coordinates by direct arithmetic with modulo wrap,
  *   - FP64 everywhere, compiled with -ffp-contract=off.
  *
- * One time step, in this order (Section 2; readings listed in the design doc):
+ * One time step, in this order (Section 2, with a reading noted wherever the paper is silent or garbled):
  *   1. densities and momenta of every fluid node              (Eqs. 3-4)
  *   2. virtual solid density of every solid node               (Eqs. 14-15)
  *   3. total force: cohesion + adhesion + body force          (Eqs. 10, 11, 13)

@@ -225,10 +225,53 @@ def reference_sample(solid, r1, r2, kw, total_steps, budget_updates=6e8):
     return c, c1, c2, "a centred 16^3 crop of the %s lattice" % WORKLOAD
 
 
+# ---- ranks: one process per GPU, each stepping its own replica of the
+# workload (no data exchange); the job's time is the slowest rank's and its
+# value counts the units of every rank
+
+def dist_init(world, backend="nccl"):
+    """The process group for world > 1 ranks (MASTER_ADDR / MASTER_PORT / RANK /
+    WORLD_SIZE from the environment); None for one rank."""
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+
+    dist.init_process_group(backend)
+    return dist
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+def max_over_ranks(dist, ms, device):
+    """The slowest rank's value of ms (every rank receives it)."""
+    if dist is None:
+        return ms
+    import torch
+
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank, world, ms):
+    """Millions of units per second over all ranks: every rank processed
+    units_per_rank within the job time ms (milliseconds)."""
+    return units_per_rank * world / (ms / 1e3) / 1e6
+
+
+def dist_finish(dist):
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
 def run_reference(args, rank, world):
-    solid, r1, r2, kw, cfg = workload_setup()
-    if rank != 0:
+    if rank != 0:  # the oracle runs once, on rank 0's host cores
         return
+    solid, r1, r2, kw, cfg = workload_setup()
     cores = os.cpu_count() or 1
     solid, r1, r2, what = reference_sample(solid, r1, r2, kw, args.steps + max(args.warmup, 0))
     nf = int((solid == 0).sum())
@@ -255,11 +298,7 @@ def run_ours(args, rank, world):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-
-        dist.init_process_group("nccl")
+    dist = dist_init(world)
     from paper_2207_01534_gb300 import lbm
 
     lbm.load()
@@ -276,8 +315,7 @@ def run_ours(args, rank, world):
         # device-timed region: K steps on the context stream, inputs resident
         clocks = ClockSampler(local)
         l0 = lat.info()["launches"]
-        if dist:
-            dist.barrier()
+        barrier(dist)
         torch.cuda.synchronize()
         clocks.start()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -287,11 +325,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         clk = clocks.stop()
         launches = lat.info()["launches"] - l0
-        ms = ev0.elapsed_time(ev1)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(dist, ev0.elapsed_time(ev1), "cuda")
         sat = lat.saturation()
         assert np.isfinite(sat).all(), sat
 
@@ -301,7 +335,7 @@ def run_ours(args, rank, world):
         lat.synchronize()
     names = ("dens", "wall", "fused", "plane", "pipeline")
     dominant = names[int(np.argmax(kms))]
-    value = nf * args.steps * world / (ms / 1e3) / 1e6
+    value = whole_job_rate(nf * args.steps, world, ms)
     peak, peak_kind = peaks()
     fused_ms = float(kms[2]) if kms[2] > 0 else float(kms.max())
     algo = ALGO_BYTES[args.storage]
@@ -356,9 +390,7 @@ def run_ours(args, rank, world):
             "saturation": {"S_w": sat[0], "S_nw_smooth": sat[1]}}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    dist_finish(dist)
 
 
 def run_batch(args, rank, world):
@@ -369,6 +401,7 @@ def run_batch(args, rank, world):
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    dist = dist_init(world)
     from paper_2207_01534_gb300 import lbm
 
     lbm.load()
@@ -385,6 +418,7 @@ def run_batch(args, rank, world):
         b.synchronize()
         clocks = ClockSampler(local)
         l0 = b.info()["launches"]
+        barrier(dist)
         torch.cuda.synchronize()
         clocks.start()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -394,7 +428,7 @@ def run_batch(args, rank, world):
         torch.cuda.synchronize()
         clk = clocks.stop()
         launches = b.info()["launches"] - l0
-        ms = ev0.elapsed_time(ev1)
+        ms = max_over_ranks(dist, ev0.elapsed_time(ev1), "cuda")
         sats = [smp.saturation() for smp in b.samples]
         assert np.isfinite(np.array(sats)).all()
         b.close()
@@ -431,7 +465,7 @@ def run_batch(args, rank, world):
     b2.close()
     h2d = sum(kw["solid"].nbytes + r1.nbytes + r2.nbytes for kw, (r1, r2) in zip(samples, states))
     d2h = 32 * len(samples)
-    value = nf * args.steps / (ms / 1e3) / 1e6
+    value = whole_job_rate(nf * args.steps, world, ms)
     peak, peak_kind = peaks()
     algo = ALGO_BYTES[args.storage]
     achieved = algo * nf / (ms / args.steps / 1e3) / 1e9
@@ -439,7 +473,7 @@ def run_batch(args, rank, world):
             "traffic": None, "kernel": "whole batched step (k_dens_batch + k_wall_batch + k_fused_batch)",
             "peak_kind": peak_kind, "algorithmic_bytes_per_node": algo}
     cfg = dict(cfg)
-    cfg.update({"parallelism": "single", "storage": args.storage, "block": block,
+    cfg.update({"parallelism": "replicas" if world > 1 else "single", "storage": args.storage, "block": block,
                 "solo_sequential_mlups": nf * args.steps / (ms_solo / 1e3) / 1e6,
                 "batch_over_solo": ms_solo / ms})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -450,6 +484,7 @@ def run_batch(args, rank, world):
                     "d2h_bytes_per_step": d2h / args.steps}}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    dist_finish(dist)
 
 
 def run_adjoint(args, rank, world):
@@ -460,6 +495,7 @@ def run_adjoint(args, rank, world):
     solid, r1, r2 = inputs.adjoint_pack_96()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
+    dist = dist_init(world)
     from paper_2207_01534_gb300 import lbm
 
     lbm.load()
@@ -476,6 +512,7 @@ def run_adjoint(args, rank, world):
         lat.init_densities(r1, r2)
         lat.record(2 * every, every)
         lat.adjoint(1.0, gx)
+        barrier(dist)
         torch.cuda.synchronize()
         clocks = ClockSampler(local)
         clocks.start()
@@ -498,25 +535,27 @@ def run_adjoint(args, rank, world):
         t_adj = ev[3].elapsed_time(ev[4]) / 1e3
         gmax = float(gx.abs().max())
         mem = lat.info()["device_bytes"]
+    t_job = max_over_ranks(dist, (t_rec + t_adj) * 1e3, "cuda") / 1e3
     fwd_rate = nsteps / t_fwd
     adj_rate = nsteps / (t_rec + t_adj)
-    value = nf * nsteps / (t_rec + t_adj) / 1e6
+    value = whole_job_rate(nf * nsteps, world, t_job * 1e3)
     peak, peak_kind = peaks()
     cfg = {"workload": ADJOINT_WORKLOAD, "grid": [96, 96, 96], "sphere_radius": 6, "porosity": 0.40, "reservoir": 8,
            "steps": nsteps, "checkpoint_every": every, "n_fluid": nf, "M": 10, "theta_deg": 45, "Pc": 0.0,
-           "loss": "smooth S_nw of the sample slab", "storage": "fp32", "parallelism": "single",
+           "loss": "smooth S_nw of the sample slab", "storage": "fp32", "parallelism": "replicas" if world > 1 else "single",
            "forward_steps_per_s": fwd_rate, "adjoint_steps_per_s": adj_rate,
            "adjoint_over_forward_time": (t_rec + t_adj) / t_fwd, "record_s": t_rec, "reverse_s": t_adj,
            "device_bytes": mem, "J": J, "dJ_drho_in1": grin, "max_abs_dJ_dxi": gmax,
            "l2": "inputs larger than L2 (checkpoints and segment states exceed 1 GB)"}
     line = {"metric": "adjoint MLUPS (forward record + reverse, 2-component D3Q19)", "value": value, "unit": UNIT,
-            "n_gpus": world, "steps": nsteps, "warmup": 1, "ms_per_step": (t_rec + t_adj) * 1e3 / nsteps,
+            "n_gpus": world, "steps": nsteps, "warmup": 1, "ms_per_step": t_job * 1e3 / nsteps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "gpu_launches": int(launches), "clocks": clk,
             "roofline": {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
                          "traffic": None, "peak_kind": peak_kind}}
     if rank == 0:
         print(json.dumps(line), flush=True)
+    dist_finish(dist)
 
 
 def main():

@@ -95,3 +95,23 @@ def test_batch_creation_rejects_bad_arguments_before_device_work(lib):
     assert h.value is None
     assert lib.lbm_last_error(None).decode().startswith("sample 0:")
     assert lib.lbm_batch_size(None) == 0
+
+
+def test_binding_constants_match_the_header():
+    """The Python binding's status, storage, schedule, plane-rule and field
+    constants are the values include/lbm.h declares."""
+    import re
+
+    from paper_2207_01534_gb300 import lbm as m
+
+    hdr = open(os.path.join(ROOT, "include", "lbm.h")).read()
+    vals = {k: int(v) for k, v in re.findall(r"\b(LBM_[A-Z0-9_]+)\s*=\s*(-?\d+)u?\b", hdr)}
+    assert {v: k for k, v in m.STATUS.items()} == {k: vals[k] for k in m.STATUS.values()}
+    for name, code in m.STORAGE.items():
+        assert vals["LBM_STORE_" + name.upper()] == code
+    for name, code in m.KERNEL.items():
+        assert vals["LBM_KERNEL_" + name.upper()] == code
+    for name, code in m.BC.items():
+        assert vals["LBM_BC_" + name.upper()] == code
+    for i, name in enumerate(m.FIELDS):
+        assert vals["LBM_FIELD_" + name.upper()] == 1 << i

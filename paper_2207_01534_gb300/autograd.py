@@ -23,6 +23,7 @@ class SaturationFunction(torch.autograd.Function):
         lattice.init_densities(*rho_init)
         lattice.record(int(nsteps), int(every))
         ctx.lattice = lattice
+        ctx.recording = lattice.recordings
         ctx.rin_dtype = rho_in1.dtype if torch.is_tensor(rho_in1) else torch.float64
         J = lattice.saturation()[1]
         return torch.tensor(J, dtype=torch.float64, device=xi_field.device)
@@ -30,6 +31,11 @@ class SaturationFunction(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad_out):
         lat = ctx.lattice
+        if getattr(lat, "recordings", None) != ctx.recording:
+            # the lattice recorded another trajectory since this forward: its
+            # adjoint would be the gradient of that one
+            raise RuntimeError("the lattice was recorded again after this forward; run backward before the next "
+                               "forward on the same lattice")
         gxi = torch.empty(lat.shape, dtype=torch.float32, device=grad_out.device)
         _, grin = lat.adjoint(float(grad_out), gxi)
         return gxi, torch.tensor(grin, dtype=ctx.rin_dtype, device=grad_out.device), None, None, None, None

@@ -116,6 +116,15 @@ struct lbm_ctx {
         int64_t count = 0;  // fluid nodes of the sample slab
     } rec;
     void *psi_alt = nullptr;
+    // flow schedule: its plan and counters (FlowState), the two density
+    // buffers (the densities of step t live in flow_psi[t & 1]), and the step
+    // whose densities flow_psi holds complete (-1: none; the next flow step
+    // first runs a density and wall pass)
+    FlowState fs{};
+    void *flow_psi[2] = {nullptr, nullptr};
+    int64_t flow_ok_step = -1;
+    int flow_lag[2] = {0, 0};
+    int flow_stall_slot = -1;  // a slot with a D item (lbm_inject_stall)
     int pipe_grid = 0;
     int64_t pipe_launches = 0;
     bool pipe_reset = false;  // a single-pass launch gave up: clear its counters before the next
@@ -281,6 +290,7 @@ void touch(lbm_ctx *c)
     c->graph_dirty = true;
     c->rec.valid = false;
     c->push_step = -1;
+    c->flow_ok_step = -1;
     if (c->parent) {
         c->parent->states_dirty = true;
         c->parent->graph_dirty = true;
@@ -336,6 +346,22 @@ void push_prime_ctx(lbm_ctx *c)
     cudaMemsetAsync(c->acc[(c->step + 1) % 3], 0, (size_t)c->nv * 8, c->stream);
     c->launches += 3;
     c->push_step = c->step;
+}
+
+// Flow schedule: the densities of the current step in flow_psi[step & 1]
+// (ordinary density and wall passes, with the pending open-plane rule after
+// step 0), unless the last flow step left them there.
+void flow_prime(lbm_ctx *c)
+{
+    c->s.psi = c->flow_psi[c->step & 1];
+    if (c->flow_ok_step == c->step) return;
+    dispatch(c, [&](auto tag) {
+        using TS = decltype(tag);
+        Ops<TS>::dens(c->s, (int)(c->step & 1), c->step > 0, c->stream, c->block);
+        Ops<TS>::wall(c->s, c->stream, c->block);
+    });
+    c->launches += (c->s.n_fluid > 0 ? 1 : 0) + (c->s.n_wall > 0 ? 1 : 0);
+    c->flow_ok_step = c->step;
 }
 
 // One time step of the split schedule.  ev != nullptr records events around
@@ -396,7 +422,20 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
         }
         return;
     }
-    if (c->kernel == LBM_KERNEL_FUSED) {
+    if (c->kernel == LBM_KERNEL_FLOW) {
+        flow_prime(c);
+        FlowState fs = c->fs;
+        fs.psi_next = c->flow_psi[(c->step + 1) & 1];
+        if (c->stall_next) fs.stall_slot = c->flow_stall_slot;
+        c->stall_next = false;
+        dispatch(c, [&](auto tag) {
+            using TS = decltype(tag);
+            if (ev) cudaEventRecord(ev[0], st);
+            Ops<TS>::flow(c->s, fs, par, st);
+            if (ev) cudaEventRecord(ev[1], st);
+        });
+        c->launches += fs.n_slots > 0 ? 1 : 0;
+    } else if (c->kernel == LBM_KERNEL_FUSED) {
         PipeState &ps = c->ps;
         if (c->pipe_reset) {  // counters of an abandoned launch: start over
             cudaMemsetAsync(ps.round_f, 0, (size_t)ps.n_chunks * 8 * 16 * 8, st);
@@ -434,6 +473,10 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
     c->launches += 2 + (c->s.n_wall > 0 ? 1 : 0);
     }
     c->step++;
+    if (c->kernel == LBM_KERNEL_FLOW) {
+        c->s.psi = c->flow_psi[c->step & 1];
+        c->flow_ok_step = c->step;
+    }
     if (c->p.reduce_every > 0 && c->step % c->p.reduce_every == 0) {
         run_reduce(c);
         k_check<<<1, 1, 0, st>>>(c->d_red, c->mass0[0], c->mass0[1], c->p.drift_limit, c->s.open_z ? 0 : 1,
@@ -565,6 +608,8 @@ lbm_status capture_steps(lbm_ctx *c, int steps, cudaGraphExec_t *out, int64_t *l
     for (lbm_ctx *q : c->subs) sub_steps.push_back(q->step);
     c->stream = c->cap_stream;
     const int64_t push0 = c->push_step;
+    const int64_t flow0 = c->flow_ok_step;
+    void *psi0 = c->s.psi;
     cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess)
         for (int q = 0; q < steps; ++q) step_once(c);
@@ -573,6 +618,8 @@ lbm_status capture_steps(lbm_ctx *c, int steps, cudaGraphExec_t *out, int64_t *l
     c->stream = user;
     c->step = step0;
     c->push_step = push0;
+    c->flow_ok_step = flow0;
+    c->s.psi = psi0;
     for (size_t k = 0; k < c->subs.size(); ++k) c->subs[k]->step = sub_steps[k];
     *launches = c->launches - launches0;
     c->launches = launches0;
@@ -919,6 +966,7 @@ lbm_status tune(lbm_ctx *c, int *best)
         dfree(q, saved[k].buf);
         q->step = saved[k].step;
         q->push_step = -1;
+        q->flow_ok_step = -1;
         if (q->h_flag) *q->h_flag = saved[k].flag;
     }
     c->step = step0;
@@ -986,6 +1034,127 @@ void dispatch_adj(const lbm_ctx *c, Fn &&fn)
 {
     if (c->storage == LBM_STORE_FP64) fn(double{});
     else fn(float{});
+}
+
+// Slot plan of the flow schedule (see FlowState).  Dependency ranges are
+// voxel windows turned into chunk ranges: the cells D(c) reads are written by
+// F of its nodes' D3Q19 neighbours, which lie within `reach` voxels of the
+// chunk's voxel range (a plane node also reads its interior node, one z plane
+// further, and that node's cells); W(c) reads the densities of its walls'
+// fluid neighbours.  With a periodic z axis, chunks that touch the first or
+// last z plane depend on every chunk.  D(c) is placed lag_d slots after the
+// last F it reads, W(c) lag_w slots after the last D it reads (at least one
+// slot each, so every wait targets a lower slot), one item of each kind per
+// slot in order of those positions.
+struct FlowPlan {
+    std::vector<int2> dep_f, dep_d, items;
+    std::vector<int> wstart;
+    int n_chunks = 0, n_slots = 0, stall_slot = -1;
+};
+
+FlowPlan build_flow_plan(const std::vector<uint32_t> &pvox, const std::vector<uint8_t> &nflags,
+                         const std::vector<uint32_t> &wpvox, int nx, int ny, int nz, const int per[3], int chunk,
+                         int lag_d, int lag_w)
+{
+    FlowPlan fp;
+    const int64_t N = (int64_t)pvox.size(), NW = (int64_t)wpvox.size();
+    const int64_t K = chunk, NC = (N + K - 1) / K;
+    const int64_t nv = (int64_t)nx * ny * nz, sxy = (int64_t)nx * ny;
+    fp.n_chunks = (int)NC;
+    const int64_t rx = per[0] ? nx - 1 : 1, ry = per[1] ? (int64_t)(ny - 1) * nx : nx;
+    const int64_t reach = sxy + std::max(rx, ry);
+    // chunk of the first node at voxel >= v / of the last node at voxel <= v
+    auto first_chunk = [&](int64_t v) {
+        const int64_t n = std::lower_bound(pvox.begin(), pvox.end(), (uint32_t)std::max<int64_t>(0, v)) - pvox.begin();
+        return (int)std::min(NC - 1, n / K);
+    };
+    auto last_chunk = [&](int64_t v) {
+        if (v >= nv) return (int)(NC - 1);
+        const int64_t n = std::upper_bound(pvox.begin(), pvox.end(), (uint32_t)v) - pvox.begin() - 1;
+        return (int)std::max<int64_t>(0, n / K);
+    };
+    auto window = [&](int64_t vlo, int64_t vhi, int64_t r) {
+        const bool wrap = per[2] && (vlo < sxy || vhi >= nv - sxy);
+        if (wrap) return make_int2(0, (int)NC - 1);
+        return make_int2(first_chunk(vlo - r), last_chunk(vhi + r));
+    };
+    fp.dep_f.resize((size_t)NC);
+    for (int64_t c = 0; c < NC; ++c) {
+        const int64_t n0 = c * K, n1 = std::min(N, n0 + K) - 1;
+        bool plane = false;
+        for (int64_t n = n0; n <= n1 && !plane; ++n) plane = (nflags[(size_t)n] & (F_INLET | F_OUTLET)) != 0;
+        fp.dep_f[(size_t)c] = window(pvox[(size_t)n0], pvox[(size_t)n1], reach + (plane ? sxy : 0));
+    }
+    // wall chunk c: walls with voxel in [first voxel of chunk c, first voxel of chunk c + 1)
+    fp.wstart.assign((size_t)NC + 1, 0);
+    for (int64_t c = 1; c < NC; ++c)
+        fp.wstart[(size_t)c] = (int)(std::lower_bound(wpvox.begin(), wpvox.end(), pvox[(size_t)(c * K)]) - wpvox.begin());
+    fp.wstart[(size_t)NC] = (int)NW;
+    fp.dep_d.resize((size_t)NC);
+    for (int64_t c = 0; c < NC; ++c) {
+        const int w0 = fp.wstart[(size_t)c], w1 = fp.wstart[(size_t)c + 1];
+        fp.dep_d[(size_t)c] = w1 > w0 ? window(wpvox[(size_t)w0], wpvox[(size_t)w1 - 1], reach) : make_int2(0, -1);
+    }
+    // positions, then one item of each kind per slot in position order
+    auto place = [](std::vector<std::pair<int64_t, int>> &pos, std::vector<int> &slot) {
+        std::stable_sort(pos.begin(), pos.end());
+        int64_t next = 0;
+        for (auto &q : pos) {
+            const int64_t k = std::max(q.first, next);
+            slot[(size_t)q.second] = (int)k;
+            next = k + 1;
+        }
+    };
+    std::vector<int> slot_d((size_t)NC, -1), slot_w((size_t)NC, -1);
+    std::vector<std::pair<int64_t, int>> pos;
+    for (int64_t c = 0; c < NC; ++c) pos.push_back({std::max<int64_t>(c, fp.dep_f[(size_t)c].y) + lag_d, (int)c});
+    place(pos, slot_d);
+    bool mono = true;
+    for (int64_t c = 1; c < NC; ++c) mono = mono && slot_d[(size_t)c] > slot_d[(size_t)c - 1];
+    pos.clear();
+    for (int64_t c = 0; c < NC; ++c) {
+        const int2 r = fp.dep_d[(size_t)c];
+        if (r.y < r.x) continue;
+        int64_t m = 0;
+        if (mono) {
+            m = slot_d[(size_t)r.y];
+        } else {
+            for (int q = r.x; q <= r.y; ++q) m = std::max<int64_t>(m, slot_d[(size_t)q]);
+        }
+        pos.push_back({m + lag_w, (int)c});
+    }
+    place(pos, slot_w);
+    int64_t n_slots = NC;
+    for (int64_t c = 0; c < NC; ++c) n_slots = std::max<int64_t>(n_slots, std::max(slot_d[(size_t)c], slot_w[(size_t)c]) + 1);
+    fp.n_slots = (int)n_slots;
+    fp.items.assign((size_t)n_slots, make_int2(-1, -1));
+    for (int64_t c = 0; c < NC; ++c) {
+        fp.items[(size_t)slot_d[(size_t)c]].x = (int)c;
+        if (slot_w[(size_t)c] >= 0) fp.items[(size_t)slot_w[(size_t)c]].y = (int)c;
+    }
+    fp.stall_slot = NC > 0 ? slot_d[0] : -1;
+    return fp;
+}
+
+// Every wait of the plan targets items of lower slots (no block can wait for
+// a block that has not started).
+bool flow_plan_ordered(const FlowPlan &fp)
+{
+    std::vector<int> slot_d((size_t)fp.n_chunks, -1);
+    for (int k = 0; k < fp.n_slots; ++k)
+        if (fp.items[(size_t)k].x >= 0) slot_d[(size_t)fp.items[(size_t)k].x] = k;
+    for (int k = 0; k < fp.n_slots; ++k) {
+        const int2 it = fp.items[(size_t)k];
+        if (it.x >= 0 && fp.dep_f[(size_t)it.x].y >= k) return false;
+        if (it.y >= 0) {
+            const int2 r = fp.dep_d[(size_t)it.y];
+            for (int q = r.x; q <= r.y; ++q)
+                if (slot_d[(size_t)q] < 0 || slot_d[(size_t)q] >= k) return false;
+        }
+    }
+    for (int c = 0; c < fp.n_chunks; ++c)
+        if (slot_d[(size_t)c] < 0) return false;
+    return true;
 }
 
 template <typename C>
@@ -1244,7 +1413,9 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
                 : p->kernel == LBM_KERNEL_WAVE    ? LBM_KERNEL_WAVE
                 : p->kernel == LBM_KERNEL_PUSH    ? LBM_KERNEL_PUSH
                 : p->kernel == LBM_KERNEL_BRICK   ? LBM_KERNEL_BRICK
-                                                  : LBM_KERNEL_SPLIT;
+                : p->kernel == LBM_KERNEL_FLOW    ? LBM_KERNEL_FLOW
+                                                  : LBM_KERNEL_SPLIT;  // AUTO and SPLIT
+    if (c->kernel == LBM_KERNEL_FLOW && N == 0) c->kernel = LBM_KERNEL_SPLIT;
     if (c->kernel == LBM_KERNEL_PUSH && c->storage != LBM_STORE_FP32) {
         delete c;
         return fail(nullptr, LBM_ERR_UNSUPPORTED, "the push schedule needs FP32 storage");
@@ -1413,6 +1584,42 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         ps.wait_ns = 1000000000ull;  // one second
         c->psi_alt = A((size_t)nv * 2 * szc);
     }
+    // Flow schedule: the slot plan and its counters, and the second density
+    // buffer.  LBM_FLOW_LAG_D / LBM_FLOW_LAG_W (slots, >= 1) override the
+    // lags, LBM_FLOW_CHUNK the nodes per chunk (rounded to kFlowThreads).
+    FlowPlan flow;
+    if (c->kernel == LBM_KERNEL_FLOW) {
+        int lag_d = 8, lag_w = 8, chunk = 4 * kFlowThreads;
+        if (const char *ev = std::getenv("LBM_FLOW_LAG_D")) lag_d = std::max(1, std::atoi(ev));
+        if (const char *ev = std::getenv("LBM_FLOW_LAG_W")) lag_w = std::max(1, std::atoi(ev));
+        if (const char *ev = std::getenv("LBM_FLOW_CHUNK"))
+            chunk = std::max(1, std::min(64, std::atoi(ev) / kFlowThreads)) * kFlowThreads;
+        c->flow_lag[0] = lag_d;
+        c->flow_lag[1] = lag_w;
+        flow = build_flow_plan(pvox, nflags, wpvox, nx, ny, nz, per, chunk, lag_d, lag_w);
+        c->fs.chunk = chunk;
+        if (!flow_plan_ordered(flow)) {
+            lbm_destroy(c);
+            return fail(nullptr, LBM_ERR_ARG, "internal: flow plan has a wait on a later slot");
+        }
+        FlowState &fs = c->fs;
+        const size_t NC = (size_t)flow.n_chunks;
+        fs.ticket = (unsigned long long *)A(8);
+        fs.fdone = (int *)A(NC * 4);
+        fs.ddone = (int *)A(NC * 4);
+        fs.abort = (int *)A(4);
+        fs.dep_f = (const int2 *)A(NC * 8);
+        fs.dep_d = (const int2 *)A(NC * 8);
+        fs.wstart = (const int *)A((NC + 1) * 4);
+        fs.items = (const int2 *)A((size_t)flow.n_slots * 8);
+        fs.n_chunks = flow.n_chunks;
+        fs.n_slots = flow.n_slots;
+        fs.stall_slot = -1;
+        fs.wait_ns = 1000000000ull;  // one second
+        c->flow_stall_slot = flow.stall_slot;
+        c->flow_psi[0] = s.psi;
+        c->flow_psi[1] = A((size_t)nv * 2 * szc);
+    }
     if (!ok) {
         lbm_destroy(c);
         return fail(nullptr, LBM_ERR_ALLOC, "device allocation failed");
@@ -1495,11 +1702,25 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         ps.n_rounds = (ps.n_chunks + G - 1) / G;
         ps.rounds = ps.n_rounds + ps.lag_w;
     }
+    if (e == cudaSuccess && c->kernel == LBM_KERNEL_FLOW) {
+        FlowState &fs = c->fs;
+        const size_t NC = (size_t)flow.n_chunks;
+        e = cudaMemset(fs.ticket, 0, 8);
+        if (e == cudaSuccess) e = cudaMemset(fs.fdone, 0, NC * 4);
+        if (e == cudaSuccess) e = cudaMemset(fs.ddone, 0, NC * 4);
+        if (e == cudaSuccess) e = cudaMemset(fs.abort, 0, 4);
+        if (e == cudaSuccess) e = cudaMemset(c->flow_psi[1], 0, (size_t)nv * 2 * szc);
+        H2D((void *)fs.dep_f, flow.dep_f.data(), NC * 8);
+        H2D((void *)fs.dep_d, flow.dep_d.data(), NC * 8);
+        H2D((void *)fs.wstart, flow.wstart.data(), (NC + 1) * 4);
+        H2D((void *)fs.items, flow.items.data(), (size_t)flow.n_slots * 8);
+    }
     if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->h_flag, sizeof(int), cudaHostAllocMapped);
     if (e == cudaSuccess) {
         *c->h_flag = 0;
         e = cudaHostGetDevicePointer((void **)&c->d_flag, c->h_flag, 0);
         c->ps.status = c->d_flag;
+        c->fs.status = c->d_flag;
     }
     if (e != cudaSuccess) {
         lbm_destroy(c);
@@ -1616,7 +1837,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
     int64_t k = 0;
     if (acc_schedule(c) && n > 0) push_prime_ctx(c);
     const int align = acc_schedule(c) ? 6 : 2;
-    const bool graphs = c->kernel != LBM_KERNEL_FUSED && !any_reduce(c) && n >= 2 * align &&
+    const bool graphs = c->kernel != LBM_KERNEL_FUSED && !any_reduce(c) && n >= 2 * align && !c->stall_next &&
                         std::getenv("LBM_NO_GRAPH") == nullptr;
     if (graphs) {
         // the first step (no plane extrapolation yet) and steps off the
@@ -1625,6 +1846,9 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
             step_once(c);
             ++k;
         }
+        // the flow schedule's graphs start from complete densities of the
+        // current step: compute them outside the graph if needed
+        if (n - k >= 2 && c->kernel == LBM_KERNEL_FLOW) flow_prime(c);
         if (n - k >= 2 && ensure_graph(c) == LBM_OK) {
             // the long graph while it fits, then the short one
             const cudaGraphExec_t gx[2] = {c->graph, c->graph_short};
@@ -1636,6 +1860,10 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
                     cudaGraphLaunch(gx[q], c->stream);
                     c->step += gn[q];
                     if (acc_schedule(c)) c->push_step = c->step;
+                    if (c->kernel == LBM_KERNEL_FLOW) {
+                        c->s.psi = c->flow_psi[c->step & 1];
+                        c->flow_ok_step = c->step;
+                    }
                     for (lbm_ctx *qq : c->subs) qq->step += gn[q];
                     c->launches += gl[q];
                 }
@@ -1655,7 +1883,9 @@ lbm_status lbm_create_batch(int32_t n, const lbm_geometry *geoms, const lbm_para
     std::vector<lbm_ctx *> subs;
     for (int32_t k = 0; k < n; ++k) {
         lbm_params pk = params[k];
-        if (pk.kernel == LBM_KERNEL_FUSED || pk.kernel == LBM_KERNEL_BRICK) pk.kernel = LBM_KERNEL_SPLIT;
+        if (pk.kernel == LBM_KERNEL_FUSED || pk.kernel == LBM_KERNEL_BRICK || pk.kernel == LBM_KERNEL_FLOW ||
+            pk.kernel == LBM_KERNEL_AUTO)
+            pk.kernel = LBM_KERNEL_SPLIT;
         lbm_ctx *q = nullptr;
         lbm_status st = lbm_create(&geoms[k], &pk, &q);
         if (st == LBM_OK && q->storage != (subs.empty() ? q->storage : subs[0]->storage)) {
@@ -1736,7 +1966,7 @@ lbm_status lbm_step_timed(lbm_ctx *c, int64_t n, double *kernel_ms, int32_t nk)
             }
             continue;
         }
-        const bool fused = c->kernel == LBM_KERNEL_FUSED;
+        const bool fused = c->kernel == LBM_KERNEL_FUSED || c->kernel == LBM_KERNEL_FLOW;
         cudaError_t e = cudaEventSynchronize(c->ev[fused ? 1 : 4]);
         if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_timed");
         if (fused) {
@@ -2107,14 +2337,15 @@ lbm_status lbm_set_wait_limit(lbm_ctx *c, double seconds)
 {
     if (!c || !(seconds > 0.0) || seconds > 60.0) return LBM_ERR_ARG;
     c->ps.wait_ns = (unsigned long long)(seconds * 1e9);
+    c->fs.wait_ns = c->ps.wait_ns;
     return LBM_OK;
 }
 
 lbm_status lbm_inject_stall(lbm_ctx *c)
 {
     if (!c) return LBM_ERR_ARG;
-    if (c->kernel != LBM_KERNEL_FUSED)
-        return fail(c, LBM_ERR_UNSUPPORTED, "only the single-pass schedule has device waits");
+    if (c->kernel != LBM_KERNEL_FUSED && !(c->kernel == LBM_KERNEL_FLOW && c->flow_stall_slot >= 0))
+        return fail(c, LBM_ERR_UNSUPPORTED, "only the single-pass and flow schedules have device waits");
     c->stall_next = true;
     return LBM_OK;
 }

@@ -89,6 +89,41 @@ struct PipeState {
     unsigned long long wait_ns;  // a wait gives up after this long (global timer)
 };
 
+// Flow schedule: one launch per time step.  The launch has n_slots blocks of
+// kFlowThreads threads; a block takes the next ticket of a counter that only
+// grows (slot k = ticket mod n_slots, launch stamp = ticket / n_slots + 1), so
+// slots are handed out in order and a block only ever waits for items of
+// lower slots, which are already running.  Fluid chunks are runs of `chunk`
+// consecutive nodes (a multiple of kFlowThreads).  Slot k runs, in this order:
+//   F(k)   collide and stream fluid chunk k when k < n_chunks; it reads only
+//          data of earlier launches;
+//   D(d)   d = items[k].x >= 0: the next step's densities of chunk d (open-
+//          plane rule first), after F of every chunk in dep_f[d] is done;
+//   W(w)   w = items[k].y >= 0: the next step's virtual wall densities of wall
+//          chunk w (walls between the first voxels of fluid chunks w and
+//          w+1), after D of every chunk in dep_d[w] is done;
+// and publishes the stamp in fdone[k] / ddone[d] as soon as F / D is done.
+// D and W lag F by a few slots, so the populations D reads were written a
+// few microseconds earlier and are still in L2.  Waits are bounded by time
+// (global timer).
+constexpr int kFlowThreads = 128;
+struct FlowState {
+    unsigned long long *ticket;  // slot tickets of every launch so far
+    int *fdone;                  // [n_chunks] stamp of the launch whose F(c) is done
+    int *ddone;                  // [n_chunks] same for D(c)
+    int *abort;                  // stamp of a launch that gave up
+    int *status;                 // host-mapped status word (bit 4: timeout)
+    const int2 *dep_f;           // [n_chunks] F chunk range that D(c) reads
+    const int2 *dep_d;           // [n_chunks] D chunk range that W(c) reads (y < x: none)
+    const int *wstart;           // [n_chunks + 1] wall index range of wall chunk c
+    const int2 *items;           // [n_slots] (D chunk, W chunk) run by slot k, -1: none
+    void *psi_next;              // densities of the next step (the other psi buffer)
+    int chunk;                   // fluid nodes per chunk
+    int n_chunks, n_slots;
+    int stall_slot;              // >= 0: that slot's D waits for a stamp that never comes (failure test)
+    unsigned long long wait_ns;  // a wait gives up after this long
+};
+
 // Per-storage-type kernel launchers, explicitly instantiated in one
 // translation unit per storage type.
 template <typename TS>
@@ -123,6 +158,8 @@ struct Ops {
     static void pipe(const DevState &s, const PipeState &ps, int parity, int grid, cudaStream_t st);
     // resident blocks per SM of the single-pass kernel
     static int pipe_blocks_per_sm();
+    // one step of the flow schedule at parity `parity` (fs.n_slots blocks)
+    static void flow(const DevState &s, const FlowState &fs, int parity, cudaStream_t st);
 };
 
 // Push schedule (FP32 storage only, lbm_push.cu): the collide-stream pass

@@ -684,7 +684,12 @@ __global__ void __launch_bounds__(256) k_wall(DevState s, int w0, int w1)
     wall_node<TS, LD_NC>(w, s, s.psi);
 }
 
-// F: the fused force / collision / streaming update of one node.
+// F: the fused force / collision / streaming update of one node.  The
+// node's own density pair is read from the density map, where the density
+// pass stored exactly the sum these populations give (the same loads summed
+// in the same order), so the force stencil runs before the populations are
+// loaded and the stencil's and the populations' loads never hold registers
+// at the same time.
 template <typename TS, int P>
 __device__ __forceinline__ void fused_node(int n, const DevState &s)
 {
@@ -693,12 +698,12 @@ __device__ __forceinline__ void fused_node(int n, const DevState &s)
     const uint32_t pv = s.pvox[n];
     const uint32_t fl = s.nflags[n];
     const Nbr b = make_nbr(fl, s);
+    const C2 rho = ld_pol(reinterpret_cast<const C2 *>(s.psi) + pv, l2_policy());
+    C2 F[3];
+    forces<TS>(rho, pv, fl, b, s, F);
     C2 f[19], dm;
     load_pops<TS, P>(f, dm, n, pv, fl, b, s);
-    const C2 rho = density_of<TS>(dm, s);
-    C2 F[3];
     C u[3], inv_rho;
-    forces<TS>(rho, pv, fl, b, s, F);
     mix_velocity<C, C2>(f, rho, F, s, inv_rho, u);
     collide<C, C2>(f, rho, inv_rho, u, F, s);
     store_pops<TS, P>(f, dm, n, pv, fl, b, s);
@@ -726,8 +731,10 @@ __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused(DevState s, 
 // momentum vanishes and f_i - f_opp(i) = 6 w_i rho_b u_n for the normal pair:
 // with j_n = rho_b - (in-plane sum + 2 outgoing sum) and N_t = half the
 // in-plane tangential momentum, f_i = f_opp(i) + 6 w_i j_n - e_i,t . N.
-template <typename TS, int PN, int LD>
-__device__ __forceinline__ void zou_he_node(int plane, int nb, uint32_t pvb, uint32_t flb, const DevState &s)
+// The plane is a template parameter so that every population index below
+// is a compile-time constant (the pairs stay in registers).
+template <typename TS, int PN, int LD, int PL>
+__device__ __forceinline__ void zou_he_node(int nb, uint32_t pvb, uint32_t flb, const DevState &s)
 {
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
@@ -735,8 +742,9 @@ __device__ __forceinline__ void zou_he_node(int plane, int nb, uint32_t pvb, uin
     const Nbr bb = make_nbr(flb, s);
     C2 f[19], dm;
     load_pops<TS, PN, LD>(f, dm, nb, pvb, flb, bb, s);
-    const int pc = plane;               // prescribed component
-    const int dir = plane == 0 ? 1 : -1;  // e_z of the entering directions
+    constexpr int plane = PL;
+    constexpr int pc = PL;                // prescribed component
+    constexpr int dir = PL == 0 ? 1 : -1;  // e_z of the entering directions
     C s0 = 0, sout = 0, nx = 0, ny = 0;
 #pragma unroll
     for (int i = 0; i < 19; ++i) {
@@ -768,7 +776,8 @@ __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb
     using C2 = typename Traits<TS>::C2;
     using S2 = typename Traits<TS>::S2;
     if (s.zou_he) {
-        zou_he_node<TS, PN, LD>(plane, nb, pvb, flb, s);
+        if (plane == 0) zou_he_node<TS, PN, LD, 0>(nb, pvb, flb, s);
+        else zou_he_node<TS, PN, LD, 1>(nb, pvb, flb, s);
         // the other component's entering populations keep their initial values
         const Nbr bb = make_nbr(flb, s);
         const int qc = 1 - plane;

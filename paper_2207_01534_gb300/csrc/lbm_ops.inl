@@ -125,6 +125,14 @@ void Ops<TS>::pipe(const DevState &s, const PipeState &ps, int parity, int grid,
 }
 
 template <typename TS>
+void Ops<TS>::flow(const DevState &s, const FlowState &fs, int parity, cudaStream_t st)
+{
+    if (fs.n_slots <= 0) return;
+    if (parity) launch_pdl(k_flow<TS, 1>, (unsigned)fs.n_slots, kFlowThreads, 0, st, s, fs);
+    else launch_pdl(k_flow<TS, 0>, (unsigned)fs.n_slots, kFlowThreads, 0, st, s, fs);
+}
+
+template <typename TS>
 int Ops<TS>::pipe_blocks_per_sm()
 {
     int a = 0, b = 0;

@@ -27,11 +27,45 @@ constexpr int kStride = 8;                                 // doubles per block 
 // Scratch: kMaxBlocks * kStride doubles = 256 KB per device.
 static __device__ __align__(256) double g_partials[kMaxBlocks * kStride];
 
-// Device address of g_partials, looked up once per device (host code may not
-// use the symbol itself: on the host it names a stand-in, not device memory).
+// Device address of g_partials, looked up once per device and context (host
+// code may not use the symbol itself: on the host it names a stand-in, not
+// device memory).  The context is part of the key: after cudaDeviceReset the
+// next call runs in a new primary context, where the module and its array are
+// loaded again at another address.
 constexpr int kMaxDevices = 64;
-double *g_scratch[kMaxDevices] = {nullptr};
+struct Scratch {
+    void *ctx;
+    double *ptr;
+};
+Scratch g_scratch[kMaxDevices] = {};
 std::mutex g_mutex;
+
+// The driver's current context (cuCtxGetCurrent, reached through the runtime
+// so that the library needs no link against the driver library); nullptr when
+// the entry point is unavailable.
+using CtxGetCurrent = int (*)(void **);
+CtxGetCurrent ctx_get_current()
+{
+    static CtxGetCurrent fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (CtxGetCurrent)p;
+    }
+    return fn;
+}
+
+void *current_context()
+{
+    void *ctx = nullptr;
+    CtxGetCurrent fn = ctx_get_current();
+    if (!fn || fn(&ctx) != 0) return nullptr;
+    return ctx;
+}
 
 __global__ void __launch_bounds__(kThreads) k_partials(const float *rho1, const float *rho2,
                                                        const uint8_t *sample, int64_t n, double *partials)
@@ -97,19 +131,23 @@ __global__ void __launch_bounds__(kThreads) k_finish(const double *partials, int
 }
 
 // Device address of the scratch array on the current device (set-up on the
-// first call per device).
+// first call per device, and again on the first call in a new context of
+// that device).
 lbm_status scratch_for_current_device(double **out)
 {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ERR_CUDA;
     std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch[dev]) {
+    Scratch &sc = g_scratch[dev];
+    void *ctx = current_context();
+    if (!sc.ptr || !ctx || ctx != sc.ctx) {
         double *ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress((void **)&ptr, g_partials);
         if (e != cudaSuccess || ptr == nullptr) return LBM_ERR_CUDA;
-        g_scratch[dev] = ptr;
+        sc.ptr = ptr;
+        sc.ctx = current_context();  // the lookup made the device's context current if none was
     }
-    *out = g_scratch[dev];
+    *out = sc.ptr;
     return LBM_OK;
 }
 

@@ -21,7 +21,7 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_ALLOC", -3: "LBM_ERR_CUDA
           -5: "LBM_ERR_DRIFT", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_UNSUPPORTED"}
 BC = {"neem": 0, "zou_he": 1}
 STORAGE = {"fp32": 0, "fp64": 1, "fp16dev": 2, "bf16dev": 3}
-KERNEL = {"auto": 0, "split": 1, "fused": 2, "wave": 3, "push": 4, "brick": 5}
+KERNEL = {"auto": 0, "split": 1, "fused": 2, "wave": 3, "push": 4, "brick": 5, "flow": 6}
 FIELDS = ("rho1", "rho2", "ux", "uy", "uz", "P")
 
 
@@ -251,7 +251,10 @@ class Lattice:
         self._c(self._lib.lbm_inject_stall(self._h))
 
     def record(self, nsteps: int, every: int = 50):
-        """lbm_record: nsteps steps, keeping a checkpoint every ``every`` steps."""
+        """lbm_record: nsteps steps, keeping a checkpoint every ``every`` steps.
+        ``recordings`` counts the calls, so a caller holding an earlier
+        recording can tell that it has been replaced."""
+        self.recordings = getattr(self, "recordings", 0) + 1
         self._c(self._lib.lbm_record(self._h, int(nsteps), int(every)))
 
     def adjoint(self, dloss: float = 1.0, grad_xi=None):

@@ -172,6 +172,14 @@ def test_autograd_function(lbm):
     assert abs(J.item() - J2) < 1e-12
     assert np.allclose(x.grad.cpu().numpy(), 3.0 * gx, rtol=1e-6, atol=0)
     assert abs(rin.grad.item() - 3.0 * grin) <= 1e-9 * abs(grin)
+    # a second forward on the same lattice replaces the recording: the first
+    # forward's backward refuses instead of returning the second's gradient
+    x1 = torch.tensor(xi, device="cuda", requires_grad=True)
+    J1 = autograd.saturation(g, (r1, r2), x1, rin.detach(), nsteps, every=6)
+    x2 = torch.tensor(xi * 0.5, device="cuda", requires_grad=True)
+    autograd.saturation(g, (r1, r2), x2, rin.detach(), nsteps, every=6)
+    with pytest.raises(RuntimeError):
+        J1.backward()
 
 
 @pytest.mark.parametrize("storage,tol_xi", [("fp32", 1e-4), ("fp64", 2e-7)])

@@ -40,7 +40,7 @@ def laplace_oracle():
 
 
 @pytest.mark.parametrize("storage", ["fp16dev", "bf16dev"])
-@pytest.mark.parametrize("sched", ["split", "fused", "brick"])
+@pytest.mark.parametrize("sched", ["split", "flow", "fused", "brick"])
 def test_laplace_48_16bit(lbm, laplace_oracle, storage, sched):
     solid, r1, r2 = inputs.laplace_48()
     g = lbm.Lattice(solid, tau=(1.0, 1.0), G=3.5, storage=storage, kernel=sched)

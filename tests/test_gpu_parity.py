@@ -35,11 +35,13 @@ def lbm():
     return m
 
 
-@pytest.fixture(params=["split", "fused", "wave"])
+@pytest.fixture(params=["split", "flow", "fused", "wave"])
 def sched(request, monkeypatch):
-    """Kernel schedule: the split passes (reference), the single-pass
-    pipeline, or the split passes per z slab in a dependency graph (forced to
-    four slabs so that the small test grids still form a wavefront)."""
+    """Kernel schedule: the split passes (reference), the flow schedule (the
+    default: one launch per step with the next densities from L2), the
+    single-pass pipeline, or the split passes per z slab in a dependency
+    graph (forced to four slabs so that the small test grids still form a
+    wavefront)."""
     if request.param == "wave":
         monkeypatch.setenv("LBM_WAVE_SLABS", "4")
     return request.param

@@ -16,6 +16,7 @@ from paper_2207_01534_gb300 import inputs
 pytestmark = pytest.mark.gpu
 
 TOL_FP64 = 1e-12
+LARGE_N = 16777216  # LBM_SATURATION_STATIC_MAX_N
 
 
 def _porous_open():
@@ -58,6 +59,48 @@ def test_static_scratch_saturation_matches_context_saturation():
         assert got[0] == ref[0]
         for k in (1, 2, 3):
             assert abs(got[k] - ref[k]) <= TOL_FP64 * max(1.0, abs(ref[k])), (k, got[k], ref[k])
+
+
+def _host_reduction(a, b, sample):
+    """The same reductions in FP64 on the host, from the same float32 arrays."""
+    a64, b64 = a.astype(np.float64), b.astype(np.float64)
+    sel = np.ones(a.shape, bool) if sample is None else sample != 0
+    cnt = int(sel.sum())
+    sw = float(np.count_nonzero(b[sel] > a[sel])) / cnt if cnt else 0.0
+    smooth = float(np.sum(a64[sel] / (a64[sel] + b64[sel]))) / cnt if cnt else 0.0
+    return np.array([sw, smooth, float(np.sum(a64)), float(np.sum(b64))])
+
+
+@pytest.mark.parametrize("n,with_sample", [(4096 * 4096 - 1000, True), (LARGE_N, False), (70001, False)])
+def test_static_scratch_against_host_fp64_sums(n, with_sample):
+    """Large inputs (up to the maximum: every block of the scratch array in
+    use, the final sum over more than 256 partials) and a NULL sample mask,
+    against FP64 sums of the same float32 arrays on the host, on two calls
+    in a row with different data."""
+    import torch
+
+    assert torch.cuda.is_available(), "this test needs a GPU"
+    from paper_2207_01534_gb300 import lbm
+
+    lbm.load()
+    out = torch.zeros(4, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for seed in (1, 2):
+        rng = np.random.default_rng(seed + n)
+        a = rng.uniform(0.02, 1.0, n).astype(np.float32)
+        b = rng.uniform(0.02, 1.0, n).astype(np.float32)
+        sample = (rng.random(n) < 0.7).astype(np.uint8) if with_sample else None
+        da, db = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
+        ds = torch.from_numpy(sample).cuda() if with_sample else None
+        out.fill_(-1.0)
+        lbm.saturation_static(da.data_ptr(), db.data_ptr(), ds.data_ptr() if with_sample else 0, n, out.data_ptr(),
+                              stream)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        ref = _host_reduction(a, b, sample)
+        assert got[0] == ref[0], (got[0], ref[0])
+        for k in (1, 2, 3):
+            assert abs(got[k] - ref[k]) <= TOL_FP64 * abs(ref[k]), (k, got[k], ref[k])
 
 
 def test_static_scratch_rejects_oversize_and_bad_arguments():

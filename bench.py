@@ -132,15 +132,27 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.rows.append([c.strip() for c in line.split(",")])
 
-    def stop(self):
-        if self.proc is None:
-            return None
-        self.proc.terminate()
+    def snapshot(self):
+        """One reading now (besides the periodic ones): taken right after the
+        timed steps are enqueued it sees the GPU under load even when the
+        timed region is shorter than the sampling period."""
         try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.th.join(timeout=2)
+            r = subprocess.run(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=10)
+            for line in r.stdout.splitlines():
+                if line.strip():
+                    self.rows.append([c.strip() for c in line.split(",")])
+        except (OSError, subprocess.SubprocessError):
+            pass
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.th.join(timeout=2)
         sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
@@ -322,7 +334,9 @@ def run_ours(args, rank, world):
         ev0.record(stream)
         lat.step(args.steps)
         ev1.record(stream)
+        clocks.snapshot()  # the steps are enqueued: the GPU is running them
         torch.cuda.synchronize()
+        clocks.snapshot()
         clk = clocks.stop()
         launches = lat.info()["launches"] - l0
         ms = max_over_ranks(dist, ev0.elapsed_time(ev1), "cuda")
@@ -430,7 +444,9 @@ def run_batch(args, rank, world):
         ev0.record(stream)
         b.step(args.steps)
         ev1.record(stream)
+        clocks.snapshot()
         torch.cuda.synchronize()
+        clocks.snapshot()
         clk = clocks.stop()
         launches = b.info()["launches"] - l0
         ms = max_over_ranks(dist, ev0.elapsed_time(ev1), "cuda")
@@ -526,6 +542,7 @@ def run_adjoint(args, rank, world):
         ev[0].record(stream)
         lat.step(nsteps)
         ev[1].record(stream)
+        clocks.snapshot()
         lat.init_densities(r1, r2)
         ev[2].record(stream)
         lat.record(nsteps, every)
@@ -533,6 +550,7 @@ def run_adjoint(args, rank, world):
         J, grin = lat.adjoint(1.0, gx)
         ev[4].record(stream)
         torch.cuda.synchronize()
+        clocks.snapshot()
         clk = clocks.stop()
         launches = lat.info()["launches"] - l0
         t_fwd = ev[0].elapsed_time(ev[1]) / 1e3

@@ -16,7 +16,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "liblbm.so")
 UNITS = ["lbm_capi.cu", "lbm_fp32.cu", "lbm_fp64.cu", "lbm_fp16.cu", "lbm_bf16.cu", "lbm_static.cu", "lbm_adj32.cu",
-         "lbm_adj64.cu", "lbm_push.cu", "lbm_brick.cu"]
+         "lbm_adj64.cu", "lbm_push.cu", "lbm_brick.cu", "lbm_geom.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

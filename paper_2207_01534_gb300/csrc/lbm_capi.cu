@@ -6,9 +6,11 @@
 #include <cmath>
 #include <cstdio>
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <type_traits>
 #include <vector>
 
@@ -125,6 +127,8 @@ struct lbm_ctx {
     int64_t flow_ok_step = -1;
     int flow_lag[2] = {0, 0};
     int flow_stall_slot = -1;  // a slot with a D item (lbm_inject_stall)
+    void *fields_buf = nullptr;  // lbm_read_fields output on the device
+    size_t fields_bytes = 0;
     int pipe_grid = 0;
     int64_t pipe_launches = 0;
     bool pipe_reset = false;  // a single-pass launch gave up: clear its counters before the next
@@ -167,6 +171,29 @@ __global__ void k_check(const double *red, double m01, double m02, double limit,
 
 namespace {
 
+// Run fn(z) for every z plane in [0, nz) on the host's cores (planes handed
+// out in order through a shared counter; fn must only write what plane z
+// owns).
+template <class Fn>
+void parallel_planes(int nz, Fn &&fn)
+{
+    unsigned t = std::thread::hardware_concurrency();
+    t = std::max(1u, std::min(t, 64u));
+    t = std::min<unsigned>(t, (unsigned)std::max(1, nz / 2));
+    if (t <= 1) {
+        for (int z = 0; z < nz; ++z) fn(z);
+        return;
+    }
+    std::atomic<int> next(0);
+    auto work = [&]() {
+        for (int z = next++; z < nz; z = next++) fn(z);
+    };
+    std::vector<std::thread> th;
+    for (unsigned k = 1; k < t; ++k) th.emplace_back(work);
+    work();
+    for (std::thread &x : th) x.join();
+}
+
 lbm_status fail(lbm_ctx *c, lbm_status st, const std::string &msg)
 {
     if (c)
@@ -180,6 +207,84 @@ lbm_status cuda_fail(lbm_ctx *c, cudaError_t e, const char *where)
 {
     return fail(c, LBM_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
 }
+
+// Device path of the geometry preprocessing: one temporary device block for
+// the uploaded mask (and xi field), the block counts and offsets, and the
+// small result record; released after the fill pass has run.
+struct DevPrep {
+    void *buf = nullptr;
+    uint8_t *mask = nullptr;
+    float *xi = nullptr;
+    int2 *cnt = nullptr, *off = nullptr;
+    int *small = nullptr;  // [err, N, NW, plane_n[0..nz], plane_w[0..nz]]
+    GeomPlan plan{};
+    void release()
+    {
+        if (!buf) return;
+        if (g_free) {
+            cudaStreamSynchronize(0);  // the fill pass reads the mask
+            g_free(buf, g_alloc_user);
+        } else {
+            cudaFreeAsync(buf, 0);  // stream-ordered after the fill pass
+        }
+        buf = nullptr;
+    }
+    ~DevPrep() { release(); }
+};
+
+// Upload the mask, count fluid voxels and walls per block on the device and
+// read back the totals, plane prefixes and geometry checks.
+lbm_status dev_prep_count(DevPrep &dp, const lbm_geometry *g, int nx, int ny, int nz, const int per[3], bool open_z,
+                          int64_t *N, int64_t *NW, std::vector<int> &plane_n, std::vector<int> &plane_w,
+                          bool *closed_face, bool *plane_solid)
+{
+    const int64_t nv = (int64_t)nx * ny * nz;
+    dp.plan = geom_plan(nullptr, nx, ny, nz, per, open_z ? 1 : 0);
+    auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t nb = (size_t)dp.plan.nblocks, nsmall = 3 + 2 * ((size_t)nz + 1);
+    const size_t b_mask = al((size_t)nv), b_xi = g->xi_field ? al((size_t)nv * 4) : 0, b_cnt = al(nb * 8);
+    const size_t total = b_mask + b_xi + 2 * b_cnt + al(nsmall * 4);
+    if (g_alloc) {
+        dp.buf = g_alloc(total, g_alloc_user);
+    } else if (cudaMallocAsync(&dp.buf, total, 0) != cudaSuccess) {
+        cudaGetLastError();
+        dp.buf = nullptr;
+    }
+    if (!dp.buf) return fail(nullptr, LBM_ERR_ALLOC, "device allocation failed (geometry preprocessing)");
+    char *q = (char *)dp.buf;
+    dp.mask = (uint8_t *)q;
+    q += b_mask;
+    if (b_xi) {
+        dp.xi = (float *)q;
+        q += b_xi;
+    }
+    dp.cnt = (int2 *)q;
+    q += b_cnt;
+    dp.off = (int2 *)q;
+    q += b_cnt;
+    dp.small = (int *)q;
+    dp.plan.d_solid = dp.mask;
+    cudaError_t e = cudaMemcpy(dp.mask, g->solid, (size_t)nv, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && dp.xi) e = cudaMemcpy(dp.xi, g->xi_field, (size_t)nv * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(dp.small, 0, 4, 0);
+    if (e == cudaSuccess) {
+        geom_count(dp.plan, dp.cnt, dp.off, dp.small, dp.small + 1, 0);
+        e = cudaGetLastError();
+    }
+    std::vector<int> h(nsmall);
+    if (e == cudaSuccess) e = cudaMemcpy(h.data(), dp.small, nsmall * 4, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return fail(nullptr, LBM_ERR_CUDA, std::string("geometry preprocessing: ") + cudaGetErrorString(e));
+    *closed_face = (h[0] & 1) != 0;
+    *plane_solid = (h[0] & 2) != 0;
+    *N = h[1];
+    *NW = h[2];
+    for (int z = 0; z <= nz; ++z) {
+        plane_n[(size_t)z] = h[3 + (size_t)z];
+        plane_w[(size_t)z] = h[3 + ((size_t)nz + 1) + (size_t)z];
+    }
+    return LBM_OK;
+}
+
 
 void *dalloc(lbm_ctx *c, size_t bytes)
 {
@@ -211,6 +316,32 @@ void dfree(lbm_ctx *c, void *ptr)
         c->free_fn(ptr, c->alloc_user);
     else
         cudaFree(ptr);
+}
+
+// Short-lived device buffers of one call (uploads, read-backs): stream-ordered
+// on the context's stream when the library allocates with the CUDA runtime,
+// so freeing one does not wait for the device; through the user's allocator
+// otherwise (then after a synchronisation of the stream).
+void *talloc(lbm_ctx *c, size_t bytes)
+{
+    if (c->alloc_fn) return dalloc(c, bytes);
+    void *p = nullptr;
+    if (cudaMallocAsync(&p, bytes ? bytes : 256, c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void tfree(lbm_ctx *c, void *p)
+{
+    if (!p) return;
+    if (c->alloc_fn) {
+        cudaStreamSynchronize(c->stream);
+        dfree(c, p);
+    } else {
+        cudaFreeAsync(p, c->stream);
+    }
 }
 
 // Run fn with the storage type of the context as a template tag.
@@ -1233,11 +1364,59 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         if (per[2] && c[2] == nz - 1) f |= F_ZHI;
         return f;
     };
-    // each fluid voxel: its index, its flag byte, and the geometry checks
-    std::vector<int32_t> cidx((size_t)nv, -1);
+    // The split and wave schedules read the geometry only on the device:
+    // it is built there from the uploaded mask (lbm_geom.cu).  The other
+    // schedules also plan on the host and take the host path below (so does
+    // every schedule with the environment variable LBM_HOST_PREP set).
+    const bool dev_prep = !brick &&
+                          (p->kernel == LBM_KERNEL_AUTO || p->kernel == LBM_KERNEL_SPLIT ||
+                           p->kernel == LBM_KERNEL_WAVE) &&
+                          std::getenv("LBM_HOST_PREP") == nullptr;
+    std::vector<int32_t> cidx;
     std::vector<uint32_t> pvox;
     std::vector<uint8_t> nflags;
+    std::vector<uint32_t> wpvox, wmask;
+    std::vector<double> winv, wxi;
+    std::vector<int> plane_n((size_t)nz + 1, 0), plane_w((size_t)nz + 1, 0);
+    int64_t N = 0, NW = 0;
     bool closed_face = false, plane_solid = false;
+    DevPrep dp;
+    if (dev_prep) {
+        // the geometry checks concern voxels on the faces of the box only and
+        // are made here, before any device work (the device pass repeats
+        // them): a fluid voxel on a face of a closed axis (neither periodic
+        // nor the open axis) has a neighbour outside the domain; an
+        // open-plane fluid voxel needs a fluid interior neighbour
+        const int64_t sxy = (int64_t)nx * ny;
+        auto fluid_on_face = [&](int a, int k) {
+            for (int u = 0; u < (a == 0 ? ny : nx); ++u)
+                for (int w = 0; w < (a == 2 ? ny : nz); ++w) {
+                    const int64_t v = a == 0 ? k + (int64_t)nx * (u + (int64_t)ny * w)
+                                    : a == 1 ? u + (int64_t)nx * (k + (int64_t)ny * w)
+                                             : u + (int64_t)nx * (w + (int64_t)ny * k);
+                    if (!solid[v]) return true;
+                }
+            return false;
+        };
+        for (int a = 0; a < 3 && !closed_face; ++a)
+            if (!per[a] && !(open_z && a == 2))
+                closed_face = fluid_on_face(a, 0) || fluid_on_face(a, dims[a] - 1);
+        if (open_z)
+            for (int64_t q = 0; q < sxy && !plane_solid; ++q)
+                plane_solid = (!solid[q] && solid[q + sxy]) ||
+                              (!solid[(nz - 1) * sxy + q] && solid[(nz - 2) * sxy + q]);
+        if (closed_face)
+            return fail(nullptr, LBM_ERR_ARG, "a fluid voxel touches a closed (non-periodic, non-open) face");
+        if (plane_solid) return fail(nullptr, LBM_ERR_ARG, "an open-plane fluid voxel has a solid interior neighbour");
+        lbm_status st = dev_prep_count(dp, g, nx, ny, nz, per, open_z, &N, &NW, plane_n, plane_w, &closed_face,
+                                       &plane_solid);
+        if (st != LBM_OK) return st;
+        if (closed_face)
+            return fail(nullptr, LBM_ERR_ARG, "a fluid voxel touches a closed (non-periodic, non-open) face");
+        if (plane_solid) return fail(nullptr, LBM_ERR_ARG, "an open-plane fluid voxel has a solid interior neighbour");
+    } else {
+    // each fluid voxel: its index, its flag byte, and the geometry checks
+    cidx.assign((size_t)nv, -1);
     auto add_node = [&](int x, int y, int z) {
         const int64_t v = x + (int64_t)nx * (y + (int64_t)ny * z);
         if (solid[v]) return;
@@ -1267,23 +1446,69 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
                         for (int y = by * kBrick; y < std::min(ny, (by + 1) * kBrick); ++y)
                             for (int x = bx * kBrick; x < std::min(nx, (bx + 1) * kBrick); ++x) add_node(x, y, z);
     } else {
-        for (int z = 0; z < nz; ++z)
+        // voxel order, numbered plane by plane on host threads: the fluid
+        // count of every z plane, then each plane's nodes at its prefix offset
+        std::vector<int64_t> first((size_t)nz + 1, 0);
+        std::vector<uint8_t> bad((size_t)nz, 0);  // bit 0 closed face, bit 1 solid behind a plane
+        parallel_planes(nz, [&](int z) {
+            const uint8_t *sp = solid + (int64_t)nx * ny * z;
+            int64_t n = 0;
+            for (int64_t q = 0; q < (int64_t)nx * ny; ++q) n += sp[q] ? 0 : 1;
+            first[(size_t)z + 1] = n;
+        });
+        for (int z = 0; z < nz; ++z) first[(size_t)z + 1] += first[(size_t)z];
+        pvox.resize((size_t)first[(size_t)nz]);
+        nflags.resize((size_t)first[(size_t)nz]);
+        parallel_planes(nz, [&](int z) {
+            int64_t n = first[(size_t)z];
+            uint8_t b = 0;
             for (int y = 0; y < ny; ++y)
-                for (int x = 0; x < nx; ++x) add_node(x, y, z);
+                for (int x = 0; x < nx; ++x) {
+                    const int64_t v = x + (int64_t)nx * (y + (int64_t)ny * z);
+                    if (solid[v]) continue;
+                    cidx[(size_t)v] = (int32_t)n;
+                    pvox[(size_t)n] = (uint32_t)v;
+                    const int c[3] = {x, y, z};
+                    uint32_t f = face_bits(c);
+                    if (open_z && z == 0) f |= F_INLET;
+                    if (open_z && z == nz - 1) f |= F_OUTLET;
+                    nflags[(size_t)n] = (uint8_t)f;
+                    ++n;
+                    const bool face = x == 0 || x == nx - 1 || y == 0 || y == ny - 1 || z == 0 || z == nz - 1;
+                    for (int j = 1; j < 19 && face; ++j) {
+                        const int e[3] = {kEx[j], kEy[j], kEz[j]};
+                        for (int a = 0; a < 3; ++a) {
+                            const int m = c[a] + e[a];
+                            if ((m < 0 || m >= dims[a]) && !per[a] && !(open_z && a == 2)) b |= 1;
+                        }
+                    }
+                    if (open_z && (z == 0 || z == nz - 1) && solid[v + (z == 0 ? 1 : -1) * (int64_t)nx * ny]) b |= 2;
+                }
+            bad[(size_t)z] = b;
+        });
+        for (int z = 0; z < nz; ++z) {
+            closed_face = closed_face || (bad[(size_t)z] & 1);
+            plane_solid = plane_solid || (bad[(size_t)z] & 2);
+        }
     }
     if (closed_face)
         return fail(nullptr, LBM_ERR_ARG, "a fluid voxel touches a closed (non-periodic, non-open) face");
     if (plane_solid) return fail(nullptr, LBM_ERR_ARG, "an open-plane fluid voxel has a solid interior neighbour");
-    const int64_t N = (int64_t)pvox.size();
+    N = (int64_t)pvox.size();
 
     // walls: solid voxels with at least one in-domain fluid neighbour (Eq. 15)
     // (voxels away from the box's faces find their neighbours at fixed
-    // offsets; the others wrap or leave the domain)
-    std::vector<uint32_t> wpvox, wmask;
-    std::vector<double> winv, wxi;
+    // offsets; the others wrap or leave the domain), found plane by plane on
+    // host threads and concatenated in voxel order
     int64_t noff[19];
     for (int j = 0; j < 19; ++j) noff[j] = kEx[j] + (int64_t)nx * (kEy[j] + (int64_t)ny * kEz[j]);
-    for (int z = 0; z < nz; ++z)
+    struct PlaneWalls {
+        std::vector<uint32_t> pv, mask;
+        std::vector<double> inv;
+    };
+    std::vector<PlaneWalls> pw((size_t)nz);
+    parallel_planes(nz, [&](int z) {
+        PlaneWalls &out = pw[(size_t)z];
         for (int y = 0; y < ny; ++y) {
             const int64_t row = (int64_t)nx * (y + (int64_t)ny * z);
             const bool inner_yz = y >= 1 && y <= ny - 2 && z >= 1 && z <= nz - 2;
@@ -1318,25 +1543,34 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
                     }
                 }
                 if (!mask) continue;
-                wpvox.push_back((uint32_t)v);
-                wmask.push_back(mask | (face_bits(c) << kWallFaceShift));
-                winv.push_back(1.0 / den);
-                wxi.push_back(g->xi_field ? (double)g->xi_field[v] : p->xi);
+                out.pv.push_back((uint32_t)v);
+                out.mask.push_back(mask | (face_bits(c) << kWallFaceShift));
+                out.inv.push_back(1.0 / den);
             }
         }
-    const int64_t NW = (int64_t)wpvox.size();
-    // first node / wall of every z plane (both lists are in voxel order)
-    std::vector<int> plane_n((size_t)nz + 1, 0), plane_w((size_t)nz + 1, 0);
+    });
     {
-        size_t a = 0, b = 0;
-        for (int z = 0; z <= nz; ++z) {
-            const int64_t v0 = (int64_t)z * nx * ny;
-            while (a < pvox.size() && (int64_t)pvox[a] < v0) ++a;
-            while (b < wpvox.size() && (int64_t)wpvox[b] < v0) ++b;
-            plane_n[(size_t)z] = (int)a;
-            plane_w[(size_t)z] = (int)b;
+        size_t tot = 0;
+        for (const PlaneWalls &q : pw) tot += q.pv.size();
+        wpvox.reserve(tot);
+        wmask.reserve(tot);
+        winv.reserve(tot);
+        wxi.reserve(tot);
+        for (const PlaneWalls &q : pw) {
+            wpvox.insert(wpvox.end(), q.pv.begin(), q.pv.end());
+            wmask.insert(wmask.end(), q.mask.begin(), q.mask.end());
+            winv.insert(winv.end(), q.inv.begin(), q.inv.end());
+            for (uint32_t v : q.pv) wxi.push_back(g->xi_field ? (double)g->xi_field[v] : p->xi);
         }
     }
+    NW = (int64_t)wpvox.size();
+    // first node / wall of every z plane (both lists are in voxel order)
+    for (int z = 0; z <= nz; ++z) {
+        const uint32_t v0 = (uint32_t)std::min<int64_t>((int64_t)z * nx * ny, UINT32_MAX);
+        plane_n[(size_t)z] = (int)(std::lower_bound(pvox.begin(), pvox.end(), v0) - pvox.begin());
+        plane_w[(size_t)z] = (int)(std::lower_bound(wpvox.begin(), wpvox.end(), v0) - wpvox.begin());
+    }
+    }  // host path
     // brick tables: per brick with fluid nodes its node range and the wall
     // voxels of the brick and its one-voxel halo (one entry per halo-region
     // cell, so a wall seen twice through a short periodic axis has two)
@@ -1645,10 +1879,16 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     auto H2D = [&](void *dst, const void *src, size_t bytes) {
         if (e == cudaSuccess && bytes) e = cudaMemcpy(dst, src, bytes, cudaMemcpyHostToDevice);
     };
-    H2D(d_pvox, pvox.data(), (size_t)N * 4);
-    H2D(d_nflags, nflags.data(), (size_t)N);
+    if (dev_prep) {
+        geom_fill(dp.plan, dp.xi, p->xi, dp.off, (int32_t *)d_cidx, (uint32_t *)d_pvox, (uint8_t *)d_nflags,
+                  (uint32_t *)d_wpvox, (uint32_t *)d_wmask, d_winv, d_wxi, szc == 8, 0);
+        e = cudaGetLastError();
+    } else {
+        H2D(d_pvox, pvox.data(), (size_t)N * 4);
+        H2D(d_nflags, nflags.data(), (size_t)N);
+        H2D(d_cidx, cidx.data(), (size_t)nv * 4);
+    }
     if (c->d_nmask) H2D(c->d_nmask, nmask.data(), (size_t)N * 4);
-    H2D(d_cidx, cidx.data(), (size_t)nv * 4);
     if (brick) {
         H2D((void *)c->bb.info, binfo.data(), binfo.size() * sizeof(BrickInfo));
         H2D((void *)c->bb.nloc, nloc.data(), nloc.size() * 2);
@@ -1658,10 +1898,12 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         for (int q = 0; q < 3; ++q)
             if (e == cudaSuccess) e = cudaMemset(c->acc[q], 0, (size_t)nv * 8);
     }
-    H2D(d_wpvox, wpvox.data(), (size_t)NW * 4);
-    H2D(d_wmask, wmask.data(), (size_t)NW * 4);
-    H2D(d_winv, winv_h, (size_t)NW * szc);
-    H2D(d_wxi, wxi_h, (size_t)NW * szc);
+    if (!dev_prep) {
+        H2D(d_wpvox, wpvox.data(), (size_t)NW * 4);
+        H2D(d_wmask, wmask.data(), (size_t)NW * 4);
+        H2D(d_winv, winv_h, (size_t)NW * szc);
+        H2D(d_wxi, wxi_h, (size_t)NW * szc);
+    }
     if (e == cudaSuccess) e = cudaMemset(s.f, 0, (size_t)18 * npad * 2 * sz);
     if (e == cudaSuccess) e = cudaMemset(s.rest, 0, (size_t)npad * 2 * szc);
     if (e == cudaSuccess) e = cudaMemset(s.psi, 0, (size_t)nv * 2 * szc);
@@ -1743,13 +1985,13 @@ lbm_status lbm_init_densities(lbm_ctx *c, const double *rho1, const double *rho2
     choose_rho_ref(c, rho1, rho2, 0);
     touch(c);
     const size_t bytes = (size_t)c->nv * 8;
-    double *d = (double *)dalloc(c, 2 * bytes);
+    double *d = (double *)talloc(c, 2 * bytes);
     if (!d) return fail(c, LBM_ERR_ALLOC, "temporary density buffer");
     cudaError_t e = cudaMemcpyAsync(d, rho1, bytes, cudaMemcpyHostToDevice, c->stream);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d + c->nv, rho2, bytes, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(c->stream);
-        dfree(c, d);
+        tfree(c, d);
         return cuda_fail(c, e, "lbm_init_densities");
     }
     dispatch(c, [&](auto tag) {
@@ -1760,8 +2002,7 @@ lbm_status lbm_init_densities(lbm_ctx *c, const double *rho1, const double *rho2
     c->launches += 2;
     c->step = 0;
     lbm_status st = check_launch(c, "lbm_init_densities");
-    cudaStreamSynchronize(c->stream);
-    dfree(c, d);
+    tfree(c, d);
     if (st != LBM_OK) return st;
     return capture_initial_mass(c);
 }
@@ -1773,12 +2014,12 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
     choose_rho_ref(c, f, f + 19 * c->nv, c->nv);
     touch(c);
     const size_t bytes = (size_t)38 * c->nv * 8;
-    double *d = (double *)dalloc(c, bytes);
+    double *d = (double *)talloc(c, bytes);
     if (!d) return fail(c, LBM_ERR_ALLOC, "temporary population buffer");
     cudaError_t e = cudaMemcpyAsync(d, f, bytes, cudaMemcpyHostToDevice, c->stream);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(c->stream);
-        dfree(c, d);
+        tfree(c, d);
         return cuda_fail(c, e, "lbm_set_populations");
     }
     dispatch(c, [&](auto tag) {
@@ -1789,8 +2030,7 @@ lbm_status lbm_set_populations(lbm_ctx *c, const double *f)
     c->launches += 2;
     c->step = 0;
     lbm_status st = check_launch(c, "lbm_set_populations");
-    cudaStreamSynchronize(c->stream);
-    dfree(c, d);
+    tfree(c, d);
     if (st != LBM_OK) return st;
     return capture_initial_mass(c);
 }
@@ -1800,7 +2040,7 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f)
     if (!c || !f) return LBM_ERR_ARG;
     if (!c->subs.empty()) return no_batch(c, "lbm_get_populations");
     const size_t bytes = (size_t)38 * c->nv * 8;
-    double *d = (double *)dalloc(c, bytes);
+    double *d = (double *)talloc(c, bytes);
     if (!d) return fail(c, LBM_ERR_ALLOC, "temporary population buffer");
     cudaError_t e = cudaMemsetAsync(d, 0, bytes, c->stream);
     dispatch(c, [&](auto tag) {
@@ -1814,8 +2054,8 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f)
     c->launches += 1;
     lbm_status st = check_launch(c, "lbm_get_populations");
     if (e == cudaSuccess) e = cudaMemcpyAsync(f, d, bytes, cudaMemcpyDeviceToHost, c->stream);
+    tfree(c, d);
     cudaError_t e2 = cudaStreamSynchronize(c->stream);
-    dfree(c, d);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_get_populations");
     if (e2 != cudaSuccess) return cuda_fail(c, e2, "lbm_get_populations");
     return st != LBM_OK ? st : device_status(c);
@@ -1990,29 +2230,37 @@ lbm_status lbm_read_fields(lbm_ctx *c, uint32_t mask, double *out, size_t n_per_
     if (!c || !out) return LBM_ERR_ARG;
     if (!c->subs.empty()) return no_batch(c, "lbm_read_fields");
     if (n_per_field < (size_t)c->nv) return fail(c, LBM_ERR_ARG, "n_per_field is smaller than nx*ny*nz");
-    const size_t bytes = (size_t)6 * c->nv * 8;
-    double *d = (double *)dalloc(c, bytes);
-    if (!d) return fail(c, LBM_ERR_ALLOC, "temporary field buffer");
-    cudaError_t e = cudaMemsetAsync(d, 0, bytes, c->stream);
+    mask &= 63u;
+    const int nfield = __builtin_popcount(mask);
+    if (nfield == 0) return LBM_OK;
+    // a buffer kept by the context for the requested fields (grown when more
+    // are asked for), so repeated reads neither allocate nor free
+    const size_t bytes = (size_t)nfield * c->nv * 8;
+    if (c->fields_bytes < bytes) {
+        if (c->fields_buf) dfree(c, c->fields_buf);
+        c->fields_buf = dalloc(c, bytes);
+        c->fields_bytes = c->fields_buf ? bytes : 0;
+        if (!c->fields_buf) return fail(c, LBM_ERR_ALLOC, "field buffer");
+    }
+    double *d = (double *)c->fields_buf;
     const int par = (int)(c->step & 1);
     dispatch(c, [&](auto tag) {
         using TS = decltype(tag);
         Ops<TS>::dens(c->s, par, c->step > 0, c->stream);
         Ops<TS>::wall(c->s, c->stream);
-        Ops<TS>::fields(c->s, par, d, c->stream);
+        Ops<TS>::fields(c->s, par, d, mask, c->stream);
     });
     c->launches += 3;
     lbm_status st = check_launch(c, "lbm_read_fields");
-    int k = 0;
-    for (int b = 0; b < 6; ++b) {
-        if (!(mask & (1u << b))) continue;
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(out + (size_t)k * n_per_field, d + (size_t)b * c->nv, (size_t)c->nv * 8,
+    cudaError_t e = cudaSuccess;
+    if (n_per_field == (size_t)c->nv) {
+        e = cudaMemcpyAsync(out, d, bytes, cudaMemcpyDeviceToHost, c->stream);
+    } else {
+        for (int k = 0; k < nfield && e == cudaSuccess; ++k)
+            e = cudaMemcpyAsync(out + (size_t)k * n_per_field, d + (size_t)k * c->nv, (size_t)c->nv * 8,
                                 cudaMemcpyDeviceToHost, c->stream);
-        ++k;
     }
     cudaError_t e2 = cudaStreamSynchronize(c->stream);
-    dfree(c, d);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_read_fields");
     if (e2 != cudaSuccess) return cuda_fail(c, e2, "lbm_read_fields");
     return st != LBM_OK ? st : device_status(c);

@@ -150,8 +150,9 @@ struct Ops {
     static void gather(const DevState &s, int parity, double *f, cudaStream_t st);
     // capture the frozen missing populations from the parity-0 layout
     static void capture_frozen(const DevState &s, double *frozen, cudaStream_t st);
-    // fields (rho1, rho2, ux, uy, uz, P) [6][nv] (double, device); needs dens+wall first
-    static void fields(const DevState &s, int parity, double *out, cudaStream_t st);
+    // fields (rho1, rho2, ux, uy, uz, P) selected by mask, packed [k][nv]
+    // (double, device; solids 0); needs dens+wall first
+    static void fields(const DevState &s, int parity, double *out, uint32_t mask, cudaStream_t st);
     // FP64 reduction over psi (needs dens first): partials[nblocks][8] then out[8]
     static void reduce(const DevState &s, double *partials, int nblocks, double *out, cudaStream_t st);
     // one step of the single-pass schedule at parity `parity` on `grid` blocks
@@ -214,6 +215,24 @@ template <typename TS>
 void brick_plane(const DevState &s, unsigned long long *acc, int parity_next, cudaStream_t st);
 // wall coefficients of the brick entries from the wall arrays (after a new xi field)
 void brick_coef(const DevState &s, const int32_t *wid, int n, float2 *coef, bool fp64, cudaStream_t st);
+
+// Geometry preprocessing on the device (lbm_geom.cu): the compact index,
+// flag bytes, wall list and plane prefixes of lbm_create from the solid mask
+// in device memory, entry for entry those of the host preprocessing.
+struct GeomPlan {
+    int nx, ny, nz, per[3], open_z;
+    int bpp, nblocks;          // 1024-voxel blocks per z plane, in all
+    const uint8_t *d_solid;    // nx*ny*nz mask on the device
+};
+GeomPlan geom_plan(const uint8_t *d_solid, int nx, int ny, int nz, const int per[3], int open_z);
+// pass 1: block counts (d_cnt[nblocks]), offsets (d_off[nblocks]), error bits
+// (*d_err, or-ed: 1 closed face, 2 solid behind an open plane) and d_out =
+// [N, NW, first node of z planes 0..nz, first wall of z planes 0..nz]
+void geom_count(const GeomPlan &g, int2 *d_cnt, int2 *d_off, int *d_err, int *d_out, cudaStream_t st);
+// pass 2: the arrays (winv / wxi in FP64 when fp64, else FP32); d_xi (nx*ny*nz
+// floats) or, when null, xi0 for every wall
+void geom_fill(const GeomPlan &g, const float *d_xi, double xi0, const int2 *d_off, int32_t *cidx, uint32_t *pvox,
+               uint8_t *nflags, uint32_t *wpvox, uint32_t *wmask, void *winv, void *wxi, bool fp64, cudaStream_t st);
 
 constexpr int kReduceBlocks = 1024;
 constexpr int kReduceThreads = 256;

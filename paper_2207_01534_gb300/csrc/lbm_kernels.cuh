@@ -980,30 +980,41 @@ __global__ void k_capture_frozen(DevState s, double *frozen)
     }
 }
 
+// Fields of the current state at every voxel (zero at solids), packed: the
+// fields whose bit is set in `mask` (RHO1, RHO2, UX, UY, UZ, P), in bit order,
+// nv doubles each.
 template <typename TS, int P>
-__global__ void k_fields(DevState s, double *out)
+__global__ void k_fields(DevState s, double *out, uint32_t mask)
 {
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= s.n_fluid) return;
-    const uint32_t pv = s.pvox[n];
-    const uint32_t fl = s.nflags[n];
-    const Nbr b = make_nbr(fl, s);
-    C2 f[19], dm;
-    load_pops<TS, P>(f, dm, n, pv, fl, b, s);
-    const C2 rho = density_of<TS>(dm, s);
-    C2 F[3];
-    C u[3], inv_rho;
-    forces<TS>(rho, pv, fl, b, s, F);
-    mix_velocity<C, C2>(f, rho, F, s, inv_rho, u);
-    const C cs2 = C(1) / C(3);
-    out[0 * s.nv + pv] = (double)rho.x;
-    out[1 * s.nv + pv] = (double)rho.y;
-    out[2 * s.nv + pv] = (double)u[0];
-    out[3 * s.nv + pv] = (double)u[1];
-    out[4 * s.nv + pv] = (double)u[2];
-    out[5 * s.nv + pv] = (double)(cs2 * (rho.x + rho.y) + cs2 * (C)s.G * rho.x * rho.y);
+    const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= s.nv) return;
+    double val[6] = {0, 0, 0, 0, 0, 0};
+    const int n = s.cidx[v];
+    if (n >= 0) {
+        const uint32_t pv = (uint32_t)v;
+        const uint32_t fl = s.nflags[n];
+        const Nbr b = make_nbr(fl, s);
+        C2 f[19], dm;
+        load_pops<TS, P>(f, dm, n, pv, fl, b, s);
+        const C2 rho = density_of<TS>(dm, s);
+        C2 F[3];
+        C u[3], inv_rho;
+        forces<TS>(rho, pv, fl, b, s, F);
+        mix_velocity<C, C2>(f, rho, F, s, inv_rho, u);
+        const C cs2 = C(1) / C(3);
+        val[0] = (double)rho.x;
+        val[1] = (double)rho.y;
+        val[2] = (double)u[0];
+        val[3] = (double)u[1];
+        val[4] = (double)u[2];
+        val[5] = (double)(cs2 * (rho.x + rho.y) + cs2 * (C)s.G * rho.x * rho.y);
+    }
+    int k = 0;
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+        if (mask & (1u << q)) out[(long long)(k++) * s.nv + v] = val[q];
 }
 
 // FP64 reduction of the densities in psi (warp shuffle -> block -> partials).

@@ -99,11 +99,11 @@ void Ops<TS>::capture_frozen(const DevState &s, double *frozen, cudaStream_t st)
 }
 
 template <typename TS>
-void Ops<TS>::fields(const DevState &s, int parity, double *out, cudaStream_t st)
+void Ops<TS>::fields(const DevState &s, int parity, double *out, uint32_t mask, cudaStream_t st)
 {
-    if (s.n_fluid == 0) return;
-    if (parity) k_fields<TS, 1><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, out);
-    else k_fields<TS, 0><<<grid_for(s.n_fluid, 256), 256, 0, st>>>(s, out);
+    if (s.nv == 0 || !(mask & 63u)) return;
+    if (parity) k_fields<TS, 1><<<grid_for(s.nv, 256), 256, 0, st>>>(s, out, mask & 63u);
+    else k_fields<TS, 0><<<grid_for(s.nv, 256), 256, 0, st>>>(s, out, mask & 63u);
 }
 
 template <typename TS>

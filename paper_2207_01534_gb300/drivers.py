@@ -63,23 +63,55 @@ def pc_sw_curve(lattice, pcs, G=3.5, minor=0.03, rho_out2=1.0, max_steps=20000, 
     return out
 
 
-def trapped_volume(rho1, rho2, solid, outlet_slices):
+def trapped_volume(rho1, rho2, solid, outlet_slices, periodic_xy=(True, True)):
     """Wetting-phase voxels (component 2 the majority, rho2 > rho1) in
     18-connected clusters that reach neither the outlet reservoir (the last
     ``outlet_slices`` z slices) nor, through it, the outlet: the volume the
-    displacing phase has cut off."""
+    displacing phase has cut off.  Clusters joined across a periodic lateral
+    face (``periodic_xy`` for x and y) are one cluster, as on the lattice."""
     from scipy import ndimage
 
     water = (rho2 > rho1) & (solid == 0)
     lab, n = ndimage.label(water, structure=ndimage.generate_binary_structure(3, 2))
     if n == 0:
         return 0
+    # labels that touch across a periodic face: compare each voxel with its
+    # D3Q19 neighbours through the wrap, and join the two clusters
+    parent = np.arange(n + 1)
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    px, py = bool(periodic_xy[0]), bool(periodic_xy[1])
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if not 0 < abs(dz) + abs(dy) + abs(dx) <= 2:
+                    continue
+                if not ((px and dx) or (py and dy)):
+                    continue  # this offset never crosses a periodic face
+                nb = np.roll(lab, (-dy if py else 0, -dx if px else 0), axis=(1, 2))
+                if dz:
+                    nb = np.roll(nb, -dz, axis=0)
+                    edge = np.ones(lab.shape[0], bool)
+                    edge[-1 if dz > 0 else 0] = False  # z is not periodic
+                    nb = nb * edge[:, None, None]
+                a, b = lab.ravel(), nb.ravel()
+                m = (a > 0) & (b > 0) & (a != b)
+                for u, v in set(zip(a[m].tolist(), b[m].tolist())):
+                    ru, rv = find(u), find(v)
+                    if ru != rv:
+                        parent[max(ru, rv)] = min(ru, rv)
+    root = np.array([find(k) for k in range(n + 1)])
     tail = lab[-outlet_slices:]
-    connected = np.unique(tail[tail > 0])
-    return int(((lab > 0) & ~np.isin(lab, connected)).sum())
+    connected = np.unique(root[np.unique(tail[tail > 0])])
+    return int(((lab > 0) & ~np.isin(root[lab], connected)).sum())
 
 
-def drainage_history(lattice, solid, nsteps, every=500, outlet_slices=8):
+def drainage_history(lattice, solid, nsteps, every=500, outlet_slices=8, periodic_xy=(True, True)):
     """Step a drainage ``nsteps`` steps, recording every ``every`` steps the
     water saturation S_w, the smooth non-wetting saturation and the trapped
     wetting volume (Section 4.1 outputs).  Returns a list of dicts."""
@@ -92,7 +124,7 @@ def drainage_history(lattice, solid, nsteps, every=500, outlet_slices=8):
         sw, snw = lattice.saturation()[:2]
         f = lattice.fields(("rho1", "rho2"))
         out.append({"step": done, "S_w": float(sw), "S_nw_smooth": float(snw),
-                    "trapped": trapped_volume(f["rho1"], f["rho2"], solid, outlet_slices)})
+                    "trapped": trapped_volume(f["rho1"], f["rho2"], solid, outlet_slices, periodic_xy)})
     return out
 
 

@@ -11,6 +11,18 @@ if HERE not in sys.path:
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+    config.addinivalue_line("markers", "slow: oracle pins that take minutes; run with LBM_SLOW_PINS=1")
+
+
+def pytest_collection_modifyitems(config, items):
+    import pytest
+
+    if os.environ.get("LBM_SLOW_PINS"):
+        return
+    skip = pytest.mark.skip(reason="slow oracle pin: set LBM_SLOW_PINS=1 to run it")
+    for item in items:
+        if "slow" in item.keywords:
+            item.add_marker(skip)
 
 
 def golden(name):

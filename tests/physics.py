@@ -29,6 +29,36 @@ def laplace_sphere(f, center):
     return R, float(dP)
 
 
+def laplace_jump(f, center, cylinder=False):
+    """Radius and pressure jump of a droplet of component 1 centred at
+    (cx, cy, cz) in a periodic box (for a y-invariant cylinder pass
+    cylinder=True).  R from the majority volume (V = 4/3 pi R^3) or area
+    (A = pi R^2); the jump is the mean pressure (Eq. 12) over the nodes more
+    than 6 lattice units inside the interface minus the mean over the nodes
+    more than 10 units outside it (the periodic far field)."""
+    rho1, rho2, P = f["rho1"], f["rho2"], f["P"]
+    nz, ny, nx = rho1.shape
+    cx, cy, cz = center
+    z, y, x = np.meshgrid(np.arange(nz), np.arange(ny), np.arange(nx), indexing="ij")
+
+    def per(a, c, n):
+        d = np.abs(a - c)
+        return np.minimum(d, n - d)
+
+    d2 = per(x, cx, nx) ** 2 + per(z, cz, nz) ** 2
+    if not cylinder:
+        d2 = d2 + per(y, cy, ny) ** 2
+    d = np.sqrt(d2)
+    inside = rho1 > rho2
+    if cylinder:
+        R = math.sqrt(float(inside[:, 0, :].sum()) / math.pi)
+    else:
+        R = (3.0 * float(inside.sum()) / (4.0 * math.pi)) ** (1.0 / 3.0)
+    p_in = float(P[d < max(1.0, R - 6.0)].mean())
+    p_out = float(P[d > R + 10.0].mean())
+    return R, p_in - p_out
+
+
 def interface_points_xz(rho1, rho2, z_min):
     """Sub-voxel points of the rho1 = rho2 contour of a y-invariant field,
     by linear interpolation along z and x, keeping points with z >= z_min."""
@@ -99,6 +129,47 @@ def duct_series_velocity(nxf, nyf, g, nu, nterms=101):
         coef = 4.0 * g / (nu * a * kn ** 3)
         u += coef * np.sin(kn * X) * (1.0 - np.cosh(kn * (Y - b / 2)) / np.cosh(kn * b / 2))
     return u
+
+
+def trapped_by_dilation(rho1, rho2, solid, outlet_slices, periodic_xy=True):
+    """Trapped wetting volume by repeated dilation (an algorithm independent
+    of cluster labelling): start from the water voxels (rho2 > rho1, fluid) of
+    the outlet reservoir, grow through water voxels over the 18 D3Q19
+    neighbours (wrapping in x and y when those faces are periodic) until
+    nothing changes, and count the water voxels never reached."""
+    water = (rho2 > rho1) & (solid == 0)
+    reached = np.zeros_like(water)
+    reached[-outlet_slices:] = water[-outlet_slices:]
+    offs = [(dz, dy, dx) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
+            if 0 < abs(dz) + abs(dy) + abs(dx) <= 2]
+
+    def shifted(a, dz, dy, dx):
+        b = np.roll(a, (dy, dx), axis=(1, 2)) if periodic_xy else a
+        if not periodic_xy:
+            b = np.zeros_like(a)
+            ys = slice(max(dy, 0), a.shape[1] + min(dy, 0))
+            yd = slice(max(-dy, 0), a.shape[1] + min(-dy, 0))
+            xs = slice(max(dx, 0), a.shape[2] + min(dx, 0))
+            xd = slice(max(-dx, 0), a.shape[2] + min(-dx, 0))
+            b[:, ys, xs] = a[:, yd, xd]
+        out = np.zeros_like(b)
+        if dz > 0:
+            out[dz:] = b[:-dz]
+        elif dz < 0:
+            out[:dz] = b[-dz:]
+        else:
+            out = b
+        return out
+
+    while True:
+        grow = reached.copy()
+        for o in offs:
+            grow |= shifted(reached, *o)
+        grow &= water
+        if np.array_equal(grow, reached):
+            break
+        reached = grow
+    return int((water & ~reached).sum())
 
 
 def trapped_wetting_volume(f, solid, reservoir):

@@ -46,17 +46,46 @@ def test_drainage_pack_128_one_step_against_the_oracle(lbm):
     assert np.abs(a1 - b1).max() <= 2e-6 and np.abs(a2 - b2).max() <= 2e-6
 
 
-def test_drainage_pack_128_history(lbm):
-    """The drainage outputs of the 128^3 configuration every 500 steps (S_w,
-    smooth S_nw, trapped wetting volume): oil enters, S_w falls."""
+@pytest.mark.parametrize("M,pc,plateau", [(10, 0.02, True), (1, 0.02, True), (10, 0.06, False)])
+def test_drainage_pack_128_history(lbm, M, pc, plateau):
+    """The drainage outputs of the 128^3 configuration over its 20,000 steps
+    (Section 4.1: S_w and the trapped wetting volume against time), for its
+    two viscosity ratios at the configured capillary pressure, and at a
+    pressure above the pore-throat entry pressure: S_w falls monotonically
+    (within 1e-4, the count's jitter) -- to a plateau at the configured
+    pressure (measured: M = 10 from 0.989 to 0.9858 by 10^4 steps, M = 1 to
+    0.9742), still falling after 20,000 steps above the entry pressure
+    (0.964 to 0.860) -- and the trapped volume of the driver equals an
+    independent count by dilation from the outlet reservoir on the same
+    fields."""
+    import physics
+
     solid, r1, r2, kw, cfg = bench.workload_setup()
+    kw = dict(kw, tau=inputs.tau_for_viscosity_ratio(float(M)), rho_in1=drivers.inlet_density(pc))
     g = lbm.Lattice(solid, sample=(8, 120), **kw)
     g.init_densities(r1, r2)
-    h = drivers.drainage_history(g, solid, 1500, every=500, outlet_slices=8)
-    print([(e["step"], round(e["S_w"], 4), e["trapped"]) for e in h])
+    h, done = [], 0
+    for s in range(1000, 20001, 1000):
+        g.step(s - done)
+        done = s
+        sw = g.saturation()[0]
+        e = {"step": s, "S_w": sw}
+        if s % 5000 == 0:
+            f = g.fields(("rho1", "rho2"))
+            e["trapped"] = drivers.trapped_volume(f["rho1"], f["rho2"], solid, 8)
+            e["trapped_dilation"] = physics.trapped_by_dilation(f["rho1"], f["rho2"], solid, 8)
+        h.append(e)
+    print("M %d Pc %.2f:" % (M, pc), [(e["step"], round(e["S_w"], 5), e.get("trapped")) for e in h])
     sw = [e["S_w"] for e in h]
-    assert sw[0] < 1.0 and all(b <= a + 1e-3 for a, b in zip(sw, sw[1:])) and sw[-1] < sw[0]
-    assert all(e["trapped"] >= 0 for e in h)
+    assert sw[-1] < sw[0] < 1.0
+    assert all(b <= a + 1e-4 for a, b in zip(sw, sw[1:]))
+    if plateau:
+        assert abs(sw[-1] - sw[-6]) < 2e-3  # the last 5000 steps
+    else:
+        assert sw[0] - sw[-1] > 0.05
+    for e in h:
+        if "trapped" in e:
+            assert e["trapped"] == e["trapped_dilation"], e
 
 
 @pytest.fixture(scope="module")
@@ -96,26 +125,59 @@ def test_rock_256_sixteen_bit_against_fp32(lbm, rock256):
 
 
 def test_rock_256_crop_against_the_oracle(lbm, rock256):
-    """A 64^3 crop of the same rock with 4-slice reservoirs: FP32 at the
-    parity bound and 16-bit storage within bounds set from its measured error
+    """A 64^3 crop of the same rock with 4-slice reservoirs against the FP64
+    oracle: the parity contract after 1000 steps (FP32 <= 1e-5, FP64 <=
+    1e-12 relative L-infinity density; measured 5.5e-7 and 6.9e-13), and
+    16-bit storage after 300 steps within bounds set from its measured error
     with a margin of about two (a front moving through a rock moves the
-    interface nodes, so the L-infinity density error is larger than for the
-    static droplet), against the FP64 oracle after 300 steps."""
+    interface nodes, so the L-infinity error is larger than for the static
+    droplet)."""
     solid = inputs.crop(rock256[0], 64, reservoir=4)
     r1, r2 = inputs.drainage_init(solid, 4)
     kw = _rock_kw()
     o = oracle.Oracle(solid, **kw)
     o.init_densities(r1, r2)
     o.step(300)
-    fo = o.fields()
-    for storage, tol in (("fp32", 1e-5), ("fp16dev", 1e-2), ("bf16dev", 5e-2)):  # measured 2e-6, 5.3e-3, 2.2e-2
+    fo300 = o.fields()
+    o.step(700)
+    fo1000 = o.fields()
+    for storage, tol, steps in (("fp32", 1e-5, 1000), ("fp64", 1e-12, 1000), ("fp16dev", 1e-2, 300),
+                                ("bf16dev", 5e-2, 300)):  # 16-bit measured 5.3e-3, 2.2e-2
+        fo = fo1000 if steps == 1000 else fo300
         g = lbm.Lattice(solid, storage=storage, **kw)
         g.init_densities(r1, r2)
-        g.step(300)
+        g.step(steps)
         fg = g.fields(("rho1", "rho2"))
         e = max(np.abs(fg[k] - fo[k]).max() / np.abs(fo[k]).max() for k in ("rho1", "rho2"))
-        print(storage, "rel L-inf %.2e" % e)
+        print(storage, steps, "steps: rel L-inf %.2e" % e)
         assert e <= tol
+
+
+def test_fp32_error_growth_on_the_rock_crop(lbm, rock256):
+    """How the FP32 path departs from the FP64 path (same kernels, FP64
+    storage and arithmetic) as a drainage front crosses the rock crop: within
+    the 1e-5 contract through 1000 steps (measured 2.2e-6 at 200 while the
+    front leaves the reservoir, 5.5e-7 at 1000), then growing as the front
+    moves through the pores (2.6e-6 at 3000, 3.0e-5 at 6000): round-off moves
+    interface nodes, and the displacement amplifies the difference."""
+    solid = inputs.crop(rock256[0], 64, reservoir=4)
+    r1, r2 = inputs.drainage_init(solid, 4)
+    kw = _rock_kw()
+    g32 = lbm.Lattice(solid, storage="fp32", **kw)
+    g64 = lbm.Lattice(solid, storage="fp64", **kw)
+    for g in (g32, g64):
+        g.init_densities(r1, r2)
+    err, done = {}, 0
+    for s in (200, 1000, 3000, 6000):
+        for g in (g32, g64):
+            g.step(s - done)
+        done = s
+        a, b = g32.fields(("rho1", "rho2")), g64.fields(("rho1", "rho2"))
+        err[s] = max(np.abs(a[k] - b[k]).max() / np.abs(b[k]).max() for k in ("rho1", "rho2"))
+    print({k: "%.2e" % v for k, v in err.items()})
+    assert err[200] <= 1e-5 and err[1000] <= 1e-5
+    assert err[6000] <= 1e-4
+    assert err[6000] > err[1000]  # the growth is real: the bound above is not vacuous
 
 
 def test_adjoint_pack_96_directional_derivative(lbm):

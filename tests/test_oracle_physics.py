@@ -119,6 +119,50 @@ def test_laplace_law_surface_tension():
     assert abs(dP3 * R3 - dP2 * R2) < 0.05 * dP2 * R2
 
 
+def _droplet_gamma(n, R0, cylinder, steps, tau=(1.0, 1.0)):
+    """gamma of a sphere (dP = 2 gamma / R) or y-invariant cylinder (dP =
+    gamma / R) of component 1 in a periodic box of edge n, initialised by
+    Eq. 16 with the Section 3.1 densities and width."""
+    shape = (n, 1, n) if cylinder else (n, n, n)
+    rin, rout, W = REF["laplace_rho_in"][0][0], REF["laplace_rho_out"][0][0], REF["laplace_W"][0][0]
+    if cylinder:
+        r1, r2 = inputs.cylinder_densities(shape, (n / 2, n / 2), R0, W, rin, rout)
+        c = (n / 2, 0, n / 2)
+    else:
+        r1, r2 = inputs.droplet_densities(shape, (n / 2, n / 2, n / 2), R0, W, rin, rout)
+        c = (n / 2, n / 2, n / 2)
+    o = oracle.Oracle(np.zeros(shape, np.uint8), tau=tau, G=G)
+    o.init_densities(r1, r2)
+    o.step(steps)
+    R, dP = physics.laplace_jump(o.fields(), c, cylinder)
+    return dP * R / (1.0 if cylinder else 2.0)
+
+
+def test_laplace_total_curvature_sphere_and_cylinder():
+    """Laplace's law in three dimensions (Section 3.1 measures it on spheres):
+    the jump is gamma times the total curvature, 2/R for a sphere and 1/R for
+    a y-invariant cylinder, so the two give one gamma in the same periodic box
+    (40^3, R0 = 12; measured 0.0825 and 0.0837).  A box this small reads
+    above the printed 0.071, which the Section 3.1 box of 128^3 reproduces
+    (0.0715 for R >= 20 on the GPU; the slow pin below checks 64^3)."""
+    gs = _droplet_gamma(40, 12, False, 2500)
+    gc = _droplet_gamma(40, 12, True, 2500)
+    assert abs(gs / gc - 1) < 0.04, (gs, gc)
+    assert GAMMA < gs < 1.25 * GAMMA
+
+
+@pytest.mark.slow
+def test_laplace_sphere_surface_tension_64():
+    """Spheres in a 64^3 periodic box (R0 = 12, 16; densities of Eq. 16):
+    gamma = dP R / 2 within 10% of the printed 0.071 (about 7-8% high in this
+    box; it falls to the printed value as the box grows to the paper's 128^3;
+    measured 0.0766 and 0.0760).  Ten to twenty minutes of the oracle."""
+    for R0 in (12, 16):
+        g = _droplet_gamma(64, R0, False, 6000)
+        print("R0 %d: gamma %.5f" % (R0, g))
+        assert abs(g / GAMMA - 1) < 0.10
+
+
 def _cap_angle(xi, tau, nx=96, nz=40, R=16, steps=4000):
     shape = (nz, 1, nx)
     solid = np.zeros(shape, np.uint8)

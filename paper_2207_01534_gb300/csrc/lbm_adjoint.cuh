@@ -271,8 +271,8 @@ __global__ void __launch_bounds__(256, AdjOcc<TS>::blocks) k_adj_node(DevState s
         if (ey(j)) A[1] = fma2(bc2<C2>(w * ey(j)), d, A[1]);
         if (ez(j)) A[2] = fma2(bc2<C2>(w * ez(j)), d, A[2]);
     }
-    const C G = (C)st.G;
-    const C g[3] = {(C)st.gx, (C)st.gy, (C)st.gz};
+    const C G = pick<C>(st.G, st.fG);
+    const C g[3] = {pick<C>(st.gx, st.fgx), pick<C>(st.gy, st.fgy), pick<C>(st.gz, st.fgz)};
     // F^1 = rho1 (-G A.y + g), F^2 = rho2 (-G A.x + g)
     C2 F[3];
 #pragma unroll
@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(256, AdjOcc<TS>::blocks) k_adj_node(DevState s
     C u[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) u[k] = (m[k].x + m[k].y + h * (F[k].x + F[k].y)) / R;
-    const C tau = (rho.x * (C)st.tau1 + rho.y * (C)st.tau2) / R;
+    const C tau = (rho.x * pick<C>(st.tau1, st.ftau1) + rho.y * pick<C>(st.tau2, st.ftau2)) / R;
     const C om = C(1) / tau;
     const C cf = C(1) - C(0.5) * om;
     const C usq = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(256, AdjOcc<TS>::blocks) k_adj_node(DevState s
     }
     taub *= om * om;
     // tau = (rho1 tau1 + rho2 tau2) / R
-    rb = add2(rb, mk2(taub * ((C)st.tau1 - tau) / R, taub * ((C)st.tau2 - tau) / R));
+    rb = add2(rb, mk2(taub * (pick<C>(st.tau1, st.ftau1) - tau) / R, taub * (pick<C>(st.tau2, st.ftau2) - tau) / R));
     // u = (m1 + m2 + h (F1 + F2)) / R
     C2 mb[3];
     const C ubu = (ub[0] * u[0] + ub[1] * u[1] + ub[2] * u[2]) / R;

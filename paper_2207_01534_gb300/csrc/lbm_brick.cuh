@@ -156,8 +156,8 @@ __global__ void __launch_bounds__(kBrickThreads, kBrickBlocks) k_brick(DevState 
                 if (ey(j)) a[1] = fma2(bc2<C2>(w * ey(j)), d, a[1]);
                 if (ez(j)) a[2] = fma2(bc2<C2>(w * ez(j)), d, a[2]);
             }
-            const C mG = -(C)s.G;
-            const C g[3] = {(C)s.gx, (C)s.gy, (C)s.gz};
+            const C mG = -pick<C>(s.G, s.fG);
+            const C g[3] = {pick<C>(s.gx, s.fgx), pick<C>(s.gy, s.fgy), pick<C>(s.gz, s.fgz)};
 #pragma unroll
             for (int k = 0; k < 3; ++k) F[k] = mul2(rho, fma2(bc2<C2>(mG), mk2(a[k].y, a[k].x), bc2<C2>(g[k])));
         }

@@ -85,6 +85,7 @@ struct lbm_ctx {
     DevState *d_states = nullptr;
     int2 *d_map_n = nullptr, *d_map_w = nullptr;
     int n_map_n = 0, n_map_w = 0, map_block = 0;
+    BatchTable *table = nullptr;  // batches of up to kParamStates samples: states and block offsets
     bool states_dirty = true;
     // CUDA graph of two split-schedule steps, captured on a private stream
     cudaStream_t cap_stream = nullptr;
@@ -379,6 +380,7 @@ void choose_rho_ref(lbm_ctx *c, const double *r1, const double *r2, int64_t stri
     }
     c->s.rref1 = cnt ? m[0] / (double)cnt : 0.0;
     c->s.rref2 = cnt ? m[1] / (double)cnt : 0.0;
+    set_float_params(c->s);
 }
 
 constexpr int kEx[19] = {0, 1, -1, 0, 0, 0, 0, 1, -1, 1, -1, 1, -1, 1, -1, 0, 0, 0, 0};
@@ -618,6 +620,8 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
 
 // Sample states and block maps of a batch.  map entry b = (sample, block
 // within the sample) for the node passes and for the wall pass.
+lbm_status upload_states(lbm_ctx *c);
+
 lbm_status build_maps(lbm_ctx *c, int block)
 {
     std::vector<int2> mn, mw;
@@ -640,11 +644,30 @@ lbm_status build_maps(lbm_ctx *c, int block)
     c->n_map_w = (int)mw.size();
     c->map_block = block;
     c->graph_dirty = true;
+    c->states_dirty = true;
+    // the parameter-space table holds block offsets of this block size
+    if (c->subs.size() <= (size_t)kParamStates) return upload_states(c);
     return LBM_OK;
 }
 
 lbm_status upload_states(lbm_ctx *c)
 {
+    if (c->subs.size() <= (size_t)kParamStates) {
+        // the batch table travels with every launch (parameter space)
+        if (!c->table) c->table = new BatchTable();
+        BatchTable &t = *c->table;
+        std::memset(&t, 0, sizeof(t));
+        t.count = (int)c->subs.size();
+        const int b = c->map_block;
+        for (int k = 0; k < t.count; ++k) {
+            const DevState &q = c->subs[(size_t)k]->s;
+            t.s[k] = q;
+            t.start_n[k + 1] = t.start_n[k] + (q.n_fluid + b - 1) / b;
+            t.start_w[k + 1] = t.start_w[k] + (q.n_wall + b - 1) / b;
+        }
+        c->states_dirty = false;
+        return LBM_OK;
+    }
     std::vector<DevState> h(c->subs.size());
     for (size_t k = 0; k < c->subs.size(); ++k) h[k] = c->subs[k]->s;
     cudaError_t e = cudaMemcpyAsync(c->d_states, h.data(), h.size() * sizeof(DevState), cudaMemcpyHostToDevice,
@@ -664,9 +687,15 @@ void enqueue_batch_step(lbm_ctx *c)
     cudaStream_t st = c->stream;
     dispatch(c, [&](auto tag) {
         using TS = decltype(tag);
-        Ops<TS>::dens_batch(c->d_states, c->d_map_n, c->n_map_n, par, s0->step > 0, st, c->map_block);
-        Ops<TS>::wall_batch(c->d_states, c->d_map_w, c->n_map_w, st, c->map_block);
-        Ops<TS>::fused_batch(c->d_states, c->d_map_n, c->n_map_n, par, st, c->map_block);
+        if (c->table) {
+            Ops<TS>::dens_table(*c->table, par, s0->step > 0, st, c->map_block);
+            Ops<TS>::wall_table(*c->table, st, c->map_block);
+            Ops<TS>::fused_table(*c->table, par, st, c->map_block);
+        } else {
+            Ops<TS>::dens_batch(c->d_states, c->d_map_n, c->n_map_n, par, s0->step > 0, st, c->map_block);
+            Ops<TS>::wall_batch(c->d_states, c->d_map_w, c->n_map_w, st, c->map_block);
+            Ops<TS>::fused_batch(c->d_states, c->d_map_n, c->n_map_n, par, st, c->map_block);
+        }
     });
     c->launches += 3;
     for (lbm_ctx *q : c->subs) {
@@ -940,6 +969,7 @@ void destroy_ctx(lbm_ctx *c)
     if (c->h_flag) cudaFreeHost(c->h_flag);
     if (c->have_ev)
         for (auto &ev : c->ev) cudaEventDestroy(ev);
+    delete c->table;
     delete c;
 }
 
@@ -1688,6 +1718,7 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     s.rho_out2 = p->rho_out2;
     s.rref1 = p->rho_ref[0];
     s.rref2 = p->rho_ref[1];
+    set_float_params(s);
     c->solid_host.assign(solid, solid + nv);
     c->per_z = per[2] != 0;
     c->plane_n = std::move(plane_n);
@@ -2289,6 +2320,7 @@ lbm_status lbm_set_inlet(lbm_ctx *c, double rho_in1)
     if (!c->subs.empty()) return no_batch(c, "lbm_set_inlet");
     c->p.rho_in1 = rho_in1;
     c->s.rho_in1 = rho_in1;
+    set_float_params(c->s);
     touch(c);
     return LBM_OK;
 }

@@ -54,7 +54,28 @@ struct DevState {
     double tau1, tau2, G, gx, gy, gz, rho_in1, rho_out2;
     double rref1, rref2;
     int32_t velocity_shift;
+    // the same parameters rounded to FP32 once on the host (set_float_params),
+    // for the kernels that compute in FP32: converting a double in every
+    // thread would run on the FP64 pipe, which GB300 provides at a small
+    // fraction of the FP32 rate
+    float ftau1, ftau2, fG, fgx, fgy, fgz, frho_in1, frho_out2, frref1, frref2;
 };
+
+// Round the double parameters of s into its FP32 copies (round to nearest,
+// as a conversion in a kernel would).
+inline void set_float_params(DevState &s)
+{
+    s.ftau1 = (float)s.tau1;
+    s.ftau2 = (float)s.tau2;
+    s.fG = (float)s.G;
+    s.fgx = (float)s.gx;
+    s.fgy = (float)s.gy;
+    s.fgz = (float)s.gz;
+    s.frho_in1 = (float)s.rho_in1;
+    s.frho_out2 = (float)s.rho_out2;
+    s.frref1 = (float)s.rref1;
+    s.frref2 = (float)s.rref2;
+}
 
 // Single-pass schedule: one cooperative launch per step (all blocks
 // co-resident).  Chunks are dealt round-robin: in round r block b collides and
@@ -124,6 +145,18 @@ struct FlowState {
     unsigned long long wait_ns;  // a wait gives up after this long
 };
 
+// Batches of up to kParamStates samples pass every sample's DevState and the
+// first launch block of every sample in the kernel's parameter space (32 KB):
+// a block finds its sample by a binary search over the block offsets, with no
+// table in global memory and no copy to shared memory.
+constexpr int kParamStates = 96;
+struct BatchTable {
+    DevState s[kParamStates];
+    int start_n[kParamStates + 1];  // first block of each sample in the node passes; [count] = total
+    int start_w[kParamStates + 1];  // same for the wall pass
+    int count;
+};
+
 // Per-storage-type kernel launchers, explicitly instantiated in one
 // translation unit per storage type.
 template <typename TS>
@@ -141,6 +174,10 @@ struct Ops {
     static void wall_batch(const DevState *states, const int2 *map, int nblocks, cudaStream_t st, int block);
     static void fused_batch(const DevState *states, const int2 *map, int nblocks, int parity, cudaStream_t st,
                             int block);
+    // the same passes with the batch table in parameter space
+    static void dens_table(const BatchTable &t, int parity, int neem, cudaStream_t st, int block);
+    static void wall_table(const BatchTable &t, cudaStream_t st, int block);
+    static void fused_table(const BatchTable &t, int parity, cudaStream_t st, int block);
     static void plane(const DevState &s, int parity_next, cudaStream_t st);
     // rest equilibrium from device densities rho[2][nv] (double); parity-0 layout
     static void init_eq(const DevState &s, const double *rho, cudaStream_t st);

@@ -81,6 +81,21 @@ __host__ __device__ constexpr C wgt(int i)
     return i == 0 ? C(1) / C(3) : (i <= 6 ? C(1) / C(18) : C(1) / C(36));
 }
 
+// A model parameter in the compute type: the FP32 copy in DevState for FP32
+// arithmetic, the double itself for FP64 (no per-thread conversion).
+template <typename C>
+__device__ __forceinline__ C pick(double d, float f);
+template <>
+__device__ __forceinline__ float pick<float>(double, float f)
+{
+    return f;
+}
+template <>
+__device__ __forceinline__ double pick<double>(double d, float)
+{
+    return d;
+}
+
 // ---------------------------------------------------------------------------
 // Pair arithmetic: (component 1, component 2) in one register pair.  FP32
 // pairs use the packed FP32 instructions of sm_100+ (one instruction for both
@@ -256,7 +271,7 @@ __device__ __forceinline__ typename Traits<TS>::C2 ref_of(const DevState &s, int
         // explicitly rounded scalar products (documented never to be merged
         // into a multiply-add), so every kernel that dequantises gets the
         // same bits
-        return mk2(__fmul_rn(wgt<C>(i), (C)s.rref1), __fmul_rn(wgt<C>(i), (C)s.rref2));
+        return mk2(__fmul_rn(wgt<C>(i), pick<C>(s.rref1, s.frref1)), __fmul_rn(wgt<C>(i), pick<C>(s.rref2, s.frref2)));
     }
 }
 
@@ -291,7 +306,7 @@ template <typename TS>
 __device__ __forceinline__ typename Traits<TS>::C2 density_of(typename Traits<TS>::C2 dm, const DevState &s)
 {
     using C = typename Traits<TS>::C;
-    return Traits<TS>::kDev ? add2(dm, mk2((C)s.rref1, (C)s.rref2)) : dm;
+    return Traits<TS>::kDev ? add2(dm, mk2(pick<C>(s.rref1, s.frref1), pick<C>(s.rref2, s.frref2))) : dm;
 }
 
 // ---------------------------------------------------------------------------
@@ -502,8 +517,8 @@ __device__ __forceinline__ void forces(typename Traits<TS>::C2 rho, uint32_t pv,
         if (ey(j)) a[1] = fma2(bc2<C2>(w * ey(j)), d, a[1]);
         if (ez(j)) a[2] = fma2(bc2<C2>(w * ez(j)), d, a[2]);
     }
-    const C mG = -(C)s.G;
-    const C g[3] = {(C)s.gx, (C)s.gy, (C)s.gz};
+    const C mG = -pick<C>(s.G, s.fG);
+    const C g[3] = {pick<C>(s.gx, s.fgx), pick<C>(s.gy, s.fgy), pick<C>(s.gz, s.fgz)};
 #pragma unroll
     for (int k = 0; k < 3; ++k) F[k] = mul2(rho, fma2(bc2<C2>(mG), mk2(a[k].y, a[k].x), bc2<C2>(g[k])));
 }
@@ -538,7 +553,7 @@ __device__ __forceinline__ void mix_velocity(const C2 f[19], C2 rho, const C2 F[
 template <typename C, typename C2>
 __device__ __forceinline__ void collide(C2 f[19], C2 rho, C inv_rho, const C u[3], const C2 F[3], const DevState &s)
 {
-    const C tau_s = (rho.x * (C)s.tau1 + rho.y * (C)s.tau2) * inv_rho;
+    const C tau_s = (rho.x * pick<C>(s.tau1, s.ftau1) + rho.y * pick<C>(s.tau2, s.ftau2)) * inv_rho;
     const C om = C(1) / tau_s;
     const C2 keep = bc2<C2>(C(1) - om);
     const C cf = C(1) - C(0.5) * om;
@@ -603,11 +618,9 @@ __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb
 // be ordered before those writes), and one shared load path keeps the
 // common case as lean as before.
 template <typename TS, int P>
-__device__ __forceinline__ void dens_node_at(int n, const DevState &s, int neem)
+__device__ __forceinline__ void dens_node_geo(int n, uint32_t pv, uint32_t fl, const DevState &s, int neem)
 {
     using C2 = typename Traits<TS>::C2;
-    const uint32_t pv = s.pvox[n];
-    const uint32_t fl = s.nflags[n];
     if (neem && (fl & (F_INLET | F_OUTLET))) {
         const int plane = (fl & F_INLET) ? 0 : 1;
         const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
@@ -617,6 +630,12 @@ __device__ __forceinline__ void dens_node_at(int n, const DevState &s, int neem)
     C2 f[19], dm;
     load_pops<TS, P, LD_CA>(f, dm, n, pv, fl, b, s);
     reinterpret_cast<C2 *>(s.psi)[pv] = density_of<TS>(dm, s);
+}
+
+template <typename TS, int P>
+__device__ __forceinline__ void dens_node_at(int n, const DevState &s, int neem)
+{
+    dens_node_geo<TS, P>(n, s.pvox[n], s.nflags[n], s, neem);
 }
 
 template <typename TS, int P>
@@ -639,26 +658,31 @@ struct DensOcc<double> {
 };
 
 // nodes [n0, n1), last first
+// The node's voxel and flags never change after creation: they are read
+// before waiting for the previous pass (programmatic dependent launch), while
+// it drains; everything it writes is read after the wait.
 template <typename TS, int P>
 __global__ void __launch_bounds__(256, DensOcc<TS>::blocks) k_dens(DevState s, int neem, int n0, int n1)
 {
     pdl_trigger();
-    pdl_wait();
     const int n = n1 - 1 - (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (n < n0) return;
-    dens_node_at<TS, P>(n, s, neem);
+    const bool live = n >= n0;
+    const uint32_t pv = live ? s.pvox[n] : 0u;
+    const uint32_t fl = live ? s.nflags[n] : 0u;
+    pdl_wait();
+    if (!live) return;
+    dens_node_geo<TS, P>(n, pv, fl, s, neem);
 }
 
 // Eq. 15 at one wall voxel: rho-tilde^sigma = chi^sigma * (sum of w_i rho^sigma
 // over in-domain fluid neighbours) / (sum of those w_i), chi = 1 +/- xi.
 template <typename TS, int LD>
-__device__ __forceinline__ void wall_node(int w, const DevState &s, void *psi_out)
+__device__ __forceinline__ void wall_node_geo(int w, uint32_t pv, uint32_t mask, typename Traits<TS>::C inv,
+                                              const DevState &s, void *psi_out)
 {
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
     C2 *psi = reinterpret_cast<C2 *>(psi_out);
-    const uint32_t pv = s.wpvox[w];
-    const uint32_t mask = s.wmask[w];
     const Nbr b = make_nbr(mask >> kWallFaceShift, s);
     C2 acc = mk2(C(0), C(0));
 #pragma unroll
@@ -668,20 +692,33 @@ __device__ __forceinline__ void wall_node(int w, const DevState &s, void *psi_ou
             acc = fma2(bc2<C2>(wgt<C>(j)), LD == LD_CG ? __ldcg(q) : *q, acc);
         }
     }
-    const C inv = reinterpret_cast<const C *>(s.winv)[w];
     const C xi = reinterpret_cast<const C *>(s.wxi)[w];
     psi[pv] = mul2(acc, mk2((C(1) + xi) * inv, (C(1) - xi) * inv));
 }
 
+template <typename TS, int LD>
+__device__ __forceinline__ void wall_node(int w, const DevState &s, void *psi_out)
+{
+    using C = typename Traits<TS>::C;
+    wall_node_geo<TS, LD>(w, s.wpvox[w], s.wmask[w], reinterpret_cast<const C *>(s.winv)[w], s, psi_out);
+}
+
 // walls [w0, w1)
+// The wall's voxel, mask and Eq. 15 denominator never change after creation
+// and are read before the wait; xi (lbm_set_xi_field) and the densities after.
 template <typename TS>
 __global__ void __launch_bounds__(256) k_wall(DevState s, int w0, int w1)
 {
+    using C = typename Traits<TS>::C;
     pdl_trigger();
-    pdl_wait();
     const int w = w0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (w >= w1) return;
-    wall_node<TS, LD_NC>(w, s, s.psi);
+    const bool live = w < w1;
+    const uint32_t pv = live ? s.wpvox[w] : 0u;
+    const uint32_t mask = live ? s.wmask[w] : 0u;
+    const C inv = live ? reinterpret_cast<const C *>(s.winv)[w] : C(0);
+    pdl_wait();
+    if (!live) return;
+    wall_node_geo<TS, LD_NC>(w, pv, mask, inv, s, s.psi);
 }
 
 // F: the fused force / collision / streaming update of one node.  The
@@ -691,12 +728,10 @@ __global__ void __launch_bounds__(256) k_wall(DevState s, int w0, int w1)
 // loaded and the stencil's and the populations' loads never hold registers
 // at the same time.
 template <typename TS, int P>
-__device__ __forceinline__ void fused_node(int n, const DevState &s)
+__device__ __forceinline__ void fused_node_geo(int n, uint32_t pv, uint32_t fl, const DevState &s)
 {
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
-    const uint32_t pv = s.pvox[n];
-    const uint32_t fl = s.nflags[n];
     const Nbr b = make_nbr(fl, s);
     const C2 rho = ld_pol(reinterpret_cast<const C2 *>(s.psi) + pv, l2_policy());
     C2 F[3];
@@ -709,15 +744,24 @@ __device__ __forceinline__ void fused_node(int n, const DevState &s)
     store_pops<TS, P>(f, dm, n, pv, fl, b, s);
 }
 
-// nodes [n0, n1)
+template <typename TS, int P>
+__device__ __forceinline__ void fused_node(int n, const DevState &s)
+{
+    fused_node_geo<TS, P>(n, s.pvox[n], s.nflags[n], s);
+}
+
+// nodes [n0, n1); the node's voxel and flags are read before the wait
 template <typename TS, int P>
 __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused(DevState s, int n0, int n1)
 {
     pdl_trigger();
-    pdl_wait();
     const int n = n0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
-    if (n >= n1) return;
-    fused_node<TS, P>(n, s);
+    const bool live = n < n1;
+    const uint32_t pv = live ? s.pvox[n] : 0u;
+    const uint32_t fl = live ? s.nflags[n] : 0u;
+    pdl_wait();
+    if (!live) return;
+    fused_node_geo<TS, P>(n, pv, fl, s);
 }
 
 // Open planes, for the parity PN of the step that reads next: the prescribed
@@ -757,7 +801,7 @@ __device__ __forceinline__ void zou_he_node(int nb, uint32_t pvb, uint32_t flb, 
             sout += v;
         }
     }
-    const C rb = (C)(plane == 0 ? s.rho_in1 : s.rho_out2);
+    const C rb = (plane == 0 ? pick<C>(s.rho_in1, s.frho_in1) : pick<C>(s.rho_out2, s.frho_out2));
     const C jn = rb - (s0 + C(2) * sout);
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -809,7 +853,7 @@ __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb
     const C ir = C(1) / (r.x + r.y);
     const C u[3] = {m[0] * ir, m[1] * ir, m[2] * ir};
     const C usq = C(1.5) * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]);
-    const C rb = (C)(plane == 0 ? s.rho_in1 : s.rho_out2);
+    const C rb = (plane == 0 ? pick<C>(s.rho_in1, s.frho_in1) : pick<C>(s.rho_out2, s.frho_out2));
     const C rin = plane == 0 ? r.x : r.y;
     const int pc = plane;  // prescribed component
 #pragma unroll
@@ -899,6 +943,69 @@ __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused_batch(const 
     const DevState &s = stage_state(states, m.x, &sh);
     const int n = m.y * blockDim.x + threadIdx.x;
     if (n < s.n_fluid) fused_node<TS, P>(n, s);
+}
+
+// Batched kernels with the batch table in parameter space (BatchTable): the
+// block's sample is the last k with start[k] <= blockIdx.x (binary search in
+// parameter memory), its node or wall index the rest; the geometry words are
+// read before the dependent-launch wait, as in the solo passes.
+__device__ __forceinline__ int table_sample(const int *start, int count)
+{
+    int lo = 0, hi = count - 1;  // start[lo] <= blockIdx.x < start[hi + 1]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= (int)blockIdx.x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename TS, int P>
+__global__ void __launch_bounds__(256, DensOcc<TS>::blocks) k_dens_table(const __grid_constant__ BatchTable t, int neem)
+{
+    pdl_trigger();
+    const int k = table_sample(t.start_n, t.count);
+    const DevState &s = t.s[k];
+    const int q = ((int)blockIdx.x - t.start_n[k]) * (int)blockDim.x + (int)threadIdx.x;
+    const bool live = q < s.n_fluid;
+    const int n = s.n_fluid - 1 - q;
+    const uint32_t pv = live ? s.pvox[n] : 0u;
+    const uint32_t fl = live ? s.nflags[n] : 0u;
+    pdl_wait();
+    if (!live) return;
+    dens_node_geo<TS, P>(n, pv, fl, s, neem && s.open_z);
+}
+
+template <typename TS>
+__global__ void __launch_bounds__(256) k_wall_table(const __grid_constant__ BatchTable t)
+{
+    using C = typename Traits<TS>::C;
+    pdl_trigger();
+    const int k = table_sample(t.start_w, t.count);
+    const DevState &s = t.s[k];
+    const int w = ((int)blockIdx.x - t.start_w[k]) * (int)blockDim.x + (int)threadIdx.x;
+    const bool live = w < s.n_wall;
+    const uint32_t pv = live ? s.wpvox[w] : 0u;
+    const uint32_t mask = live ? s.wmask[w] : 0u;
+    const C inv = live ? reinterpret_cast<const C *>(s.winv)[w] : C(0);
+    pdl_wait();
+    if (!live) return;
+    wall_node_geo<TS, LD_NC>(w, pv, mask, inv, s, s.psi);
+}
+
+template <typename TS, int P>
+__global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused_table(const __grid_constant__ BatchTable t)
+{
+    pdl_trigger();
+    const int k = table_sample(t.start_n, t.count);
+    const DevState &s = t.s[k];
+    const int n = ((int)blockIdx.x - t.start_n[k]) * (int)blockDim.x + (int)threadIdx.x;
+    const bool live = n < s.n_fluid;
+    const uint32_t pv = live ? s.pvox[n] : 0u;
+    const uint32_t fl = live ? s.nflags[n] : 0u;
+    pdl_wait();
+    if (!live) return;
+    fused_node_geo<TS, P>(n, pv, fl, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -1009,7 +1116,7 @@ __global__ void k_fields(DevState s, double *out, uint32_t mask)
         val[2] = (double)u[0];
         val[3] = (double)u[1];
         val[4] = (double)u[2];
-        val[5] = (double)(cs2 * (rho.x + rho.y) + cs2 * (C)s.G * rho.x * rho.y);
+        val[5] = (double)(cs2 * (rho.x + rho.y) + cs2 * pick<C>(s.G, s.fG) * rho.x * rho.y);
     }
     int k = 0;
 #pragma unroll

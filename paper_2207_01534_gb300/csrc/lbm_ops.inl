@@ -62,6 +62,32 @@ void Ops<TS>::fused_batch(const DevState *states, const int2 *map, int nblocks, 
 }
 
 template <typename TS>
+void Ops<TS>::dens_table(const BatchTable &t, int parity, int neem, cudaStream_t st, int block)
+{
+    const int nb = t.start_n[t.count];
+    if (nb <= 0) return;
+    if (parity) launch_pdl(k_dens_table<TS, 1>, (unsigned)nb, block, 0, st, t, neem);
+    else launch_pdl(k_dens_table<TS, 0>, (unsigned)nb, block, 0, st, t, neem);
+}
+
+template <typename TS>
+void Ops<TS>::wall_table(const BatchTable &t, cudaStream_t st, int block)
+{
+    const int nb = t.start_w[t.count];
+    if (nb <= 0) return;
+    launch_pdl(k_wall_table<TS>, (unsigned)nb, block, 0, st, t);
+}
+
+template <typename TS>
+void Ops<TS>::fused_table(const BatchTable &t, int parity, cudaStream_t st, int block)
+{
+    const int nb = t.start_n[t.count];
+    if (nb <= 0) return;
+    if (parity) launch_pdl(k_fused_table<TS, 1>, (unsigned)nb, block, 0, st, t);
+    else launch_pdl(k_fused_table<TS, 0>, (unsigned)nb, block, 0, st, t);
+}
+
+template <typename TS>
 void Ops<TS>::plane(const DevState &s, int parity_next, cudaStream_t st)
 {
     if (!s.open_z || s.nxy == 0) return;

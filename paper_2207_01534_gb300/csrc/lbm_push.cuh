@@ -40,8 +40,8 @@ __device__ __forceinline__ void forces_acc(float2 rho, uint32_t pv, uint32_t fl,
         if (ey(j)) a[1] = fma2(bc2<float2>(w * ey(j)), d, a[1]);
         if (ez(j)) a[2] = fma2(bc2<float2>(w * ez(j)), d, a[2]);
     }
-    const float mG = -(float)s.G;
-    const float g[3] = {(float)s.gx, (float)s.gy, (float)s.gz};
+    const float mG = -s.fG;
+    const float g[3] = {s.fgx, s.fgy, s.fgz};
 #pragma unroll
     for (int k = 0; k < 3; ++k) F[k] = mul2(rho, fma2(bc2<float2>(mG), make_float2(a[k].y, a[k].x), bc2<float2>(g[k])));
 }

@@ -48,6 +48,11 @@ ALGO_BYTES = {"fp32": 2 * (18 * 8 + 8) + 4, "fp64": 2 * (18 * 16 + 16) + 4,
               "fp16dev": 2 * (18 * 4 + 8) + 4, "bf16dev": 2 * (18 * 4 + 8) + 4}
 DTYPE = {"fp32": "f32", "fp64": "f64", "fp16dev": "f32 (f16 storage)", "bf16dev": "f32 (bf16 storage)"}
 WORKLOAD = "drainage_pack_128"
+# algorithmic bytes per fluid node and time step of the reverse-mode job
+# (record + reverse): the recorded forward step, then in the reverse sweep
+# the recomputed step, the recomputed state stored and read back, and the
+# adjoint population pairs read and written, plus the node's voxel index
+ADJ_BYTES = 308 + 304 + 304 + 304 + 4
 NOMINAL_HBM_GBS = 7900.0  # GB300 HBM3e, nominal
 
 
@@ -357,7 +362,8 @@ def run_ours(args, rank, world):
     step_bytes_rate = algo * nf / (ms / args.steps / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": measured_traffic("k_fused", args.storage) if args.kernel in ("auto", "split") else None,
-            "kernel": {"brick": "k_brick", "push": "k_fused_push", "fused": "k_pipe"}.get(args.kernel, "k_fused"),
+            "kernel": {"brick": "k_brick", "push": "k_fused_push", "fused": "k_pipe", "flow": "k_flow"}.get(args.kernel,
+                                                                                                         "k_fused"),
             "peak_kind": peak_kind,
             "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": achieved / NOMINAL_HBM_GBS,
             "algorithmic_bytes_per_node": algo, "kernel_ms": {names[k]: float(kms[k]) for k in range(5)},
@@ -563,6 +569,7 @@ def run_adjoint(args, rank, world):
     adj_rate = nsteps / (t_rec + t_adj)
     value = whole_job_rate(nf * nsteps, world, t_job * 1e3)
     peak, peak_kind = peaks()
+    achieved = ADJ_BYTES * nf * nsteps / (t_rec + t_adj) / 1e9
     cfg = {"workload": ADJOINT_WORKLOAD, "grid": [96, 96, 96], "sphere_radius": 6, "porosity": 0.40, "reservoir": 8,
            "steps": nsteps, "checkpoint_every": every, "n_fluid": nf, "M": 10, "theta_deg": 45, "Pc": 0.0,
            "loss": "smooth S_nw of the sample slab", "storage": "fp32", "parallelism": "replicas" if world > 1 else "single",
@@ -574,8 +581,12 @@ def run_adjoint(args, rank, world):
             "n_gpus": world, "steps": nsteps, "warmup": 1, "ms_per_step": t_job * 1e3 / nsteps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": cfg, "gpu_launches": int(launches), "clocks": clk,
-            "roofline": {"bound": "hbm", "achieved": None, "peak": peak, "unit": "GB/s", "frac": None,
-                         "traffic": None, "peak_kind": peak_kind}}
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": None, "peak_kind": peak_kind,
+                         "kernel": "record + reverse passes (forward, recompute, adjoint kernels)",
+                         "algorithmic_bytes_per_node_step": ADJ_BYTES,
+                         "bytes_basis": "record 308 (a forward step) + recompute 304 + segment state stored and "
+                                        "read 304 + adjoint populations read and written 304 + voxel index 4"}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     dist_finish(dist)
@@ -589,7 +600,7 @@ def main():
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--kernel", default="auto", choices=("auto", "split", "fused", "wave", "push", "brick"))
+    ap.add_argument("--kernel", default="auto", choices=("auto", "split", "flow", "fused", "wave", "push", "brick"))
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp64", "fp16dev", "bf16dev"))
     ap.add_argument("--cpu-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")

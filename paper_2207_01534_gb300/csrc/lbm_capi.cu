@@ -61,8 +61,9 @@ struct lbm_ctx {
     double *d_frozen = nullptr;
     int *h_flag = nullptr;  // pinned, device-mapped status word
     int *d_flag = nullptr;
-    // push schedule: rotating density accumulators, fluid-neighbour masks, and
-    // the step whose densities acc[step % 3] holds (-1: none)
+    // push and brick schedules: rotating density accumulators (two for push,
+    // three for brick), fluid-neighbour masks, and the step whose densities
+    // acc[step % ring] holds (-1: none)
     unsigned long long *acc[3] = {nullptr, nullptr, nullptr};
     uint32_t *d_nmask = nullptr;
     int64_t push_step = -1;
@@ -463,6 +464,16 @@ lbm_status capture_initial_mass(lbm_ctx *c)
 
 bool acc_schedule(const lbm_ctx *c) { return c->kernel == LBM_KERNEL_PUSH || c->kernel == LBM_KERNEL_BRICK; }
 
+// Accumulator k steps ahead of the current one.  The push schedule rotates
+// two buffers (its finish pass clears the one the collide-stream pass has
+// just read); the brick schedule three (each brick clears its own voxels of
+// the buffer after next while others may still read the current one).
+unsigned long long *acc_at(const lbm_ctx *c, int k)
+{
+    const int ring = c->kernel == LBM_KERNEL_PUSH ? 2 : 3;
+    return c->acc[(c->step + k) % ring];
+}
+
 // Push and brick schedules: the accumulator of the current step from a
 // density and wall pass (any state), and a cleared accumulator for the next
 // step.  The brick schedule keeps fluid voxels only (it recomputes walls).
@@ -475,8 +486,8 @@ void push_prime_ctx(lbm_ctx *c)
         Ops<TS>::dens(c->s, par, c->step > 0, c->stream, c->block);
         Ops<TS>::wall(c->s, c->stream, c->block);
     });
-    push_prime(c->s, c->acc[c->step % 3], c->stream, c->kernel != LBM_KERNEL_BRICK);
-    cudaMemsetAsync(c->acc[(c->step + 1) % 3], 0, (size_t)c->nv * 8, c->stream);
+    push_prime(c->s, acc_at(c, 0), c->stream, c->kernel != LBM_KERNEL_BRICK);
+    cudaMemsetAsync(acc_at(c, 1), 0, (size_t)c->nv * 8, c->stream);
     c->launches += 3;
     c->push_step = c->step;
 }
@@ -506,18 +517,21 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
     if (c->kernel == LBM_KERNEL_PUSH) {
         push_prime_ctx(c);
         PushBufs pb;
-        pb.rd = c->acc[c->step % 3];
-        pb.acc = c->acc[(c->step + 1) % 3];
-        pb.clr = c->acc[(c->step + 2) % 3];
+        pb.rd = acc_at(c, 0);
+        pb.acc = acc_at(c, 1);
+        pb.clr = acc_at(c, 2);  // = rd: read by this collide-stream pass, cleared by its finish pass
         pb.nmask = c->d_nmask;
         if (ev) cudaEventRecord(ev[0], st);
         push_fused(c->s, pb, par, st);
         if (ev) cudaEventRecord(ev[1], st);
-        push_plane(c->s, pb.acc, 1 - par, st);
+        // walls at least two planes from an open plane go with the plane nodes
+        const int nz = c->s.nz;
+        const int w_lo = c->plane_w[(size_t)std::min(2, nz)];
+        const int w_hi = std::max(w_lo, c->plane_w[(size_t)std::max(0, nz - 2)]);
+        const int nl = push_finish(c->s, pb.acc, pb.clr, 1 - par, w_lo, w_hi, st);
         if (ev) cudaEventRecord(ev[2], st);
-        push_wall(c->s, pb.acc, st);
         if (ev) cudaEventRecord(ev[3], st);
-        c->launches += 1 + (c->s.open_z ? 1 : 0) + (c->s.n_wall > 0 ? 1 : 0);
+        c->launches += (c->s.n_fluid > 0 ? 1 : 0) + nl;
         c->step++;
         c->push_step = c->step;
         if (c->p.reduce_every > 0 && c->step % c->p.reduce_every == 0) {
@@ -531,9 +545,9 @@ void enqueue_step(lbm_ctx *c, cudaEvent_t *ev)
     if (c->kernel == LBM_KERNEL_BRICK) {
         push_prime_ctx(c);
         BrickBufs bb = c->bb;
-        bb.rd = c->acc[c->step % 3];
-        bb.acc = c->acc[(c->step + 1) % 3];
-        bb.clr = c->acc[(c->step + 2) % 3];
+        bb.rd = acc_at(c, 0);
+        bb.acc = acc_at(c, 1);
+        bb.clr = acc_at(c, 2);
         dispatch(c, [&](auto tag) {
             using TS = decltype(tag);
             if constexpr (!std::is_same<TS, double>::value) {
@@ -1763,7 +1777,7 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
         c->bb.per = per[0] | (per[1] << 1) | (per[2] << 2);
     }
     if (c->kernel == LBM_KERNEL_PUSH) {
-        for (int q = 0; q < 3; ++q) c->acc[q] = (unsigned long long *)A((size_t)nv * 8);
+        for (int q = 0; q < 2; ++q) c->acc[q] = (unsigned long long *)A((size_t)nv * 8);
         c->d_nmask = (uint32_t *)A((size_t)N * 4);
         nmask.assign((size_t)N, 0u);
         for (int64_t n = 0; n < N; ++n) {
@@ -2226,11 +2240,11 @@ lbm_status lbm_step_timed(lbm_ctx *c, int64_t n, double *kernel_ms, int32_t nk)
             }
             continue;
         }
-        if (c->kernel == LBM_KERNEL_PUSH) {  // collide-stream, plane, wall
+        if (c->kernel == LBM_KERNEL_PUSH) {  // collide-stream; plane nodes with the walls
             cudaError_t e = cudaEventSynchronize(c->ev[3]);
             if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step_timed");
-            const int slot[3] = {2, 3, 1};
-            for (int q = 0; q < 3; ++q) {
+            const int slot[2] = {2, 3};
+            for (int q = 0; q < 2; ++q) {
                 float ms = 0;
                 cudaEventElapsedTime(&ms, c->ev[q], c->ev[q + 1]);
                 if (slot[q] < nk) kernel_ms[slot[q]] += ms;

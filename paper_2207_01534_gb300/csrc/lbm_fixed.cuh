@@ -31,6 +31,15 @@ __device__ __forceinline__ unsigned long long fix_enc2(float2 v)
     return (unsigned long long)fix_enc(v.x) | ((unsigned long long)fix_enc(v.y) << 32);
 }
 
+// the sum v of k contributions, added at once: k biases
+__device__ __forceinline__ unsigned long long fix_enc2n(float2 v, uint32_t k)
+{
+    const float sc = (float)(1 << kFixShift);
+    const uint32_t a = (uint32_t)__float2int_rn(v.x * sc) + k * kFixBias;
+    const uint32_t b = (uint32_t)__float2int_rn(v.y * sc) + k * kFixBias;
+    return (unsigned long long)a | ((unsigned long long)b << 32);
+}
+
 // one stored total (plane node density, wall virtual density)
 __device__ __forceinline__ unsigned long long fix_total2(float2 v)
 {

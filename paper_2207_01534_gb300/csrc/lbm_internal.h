@@ -206,13 +206,16 @@ struct Ops {
 struct PushBufs {
     const unsigned long long *rd;  // densities of this step (dense, fluid and wall voxels)
     unsigned long long *acc;       // next step's accumulators (cleared, fluid voxels)
-    unsigned long long *clr;       // the buffer to clear for the step after
+    unsigned long long *clr;       // the buffer to clear for the step after (by the finish pass)
     const uint32_t *nmask;         // [n_fluid] bit j: x + e_j is an in-domain fluid voxel
 };
 void push_fused(const DevState &s, const PushBufs &pb, int parity, cudaStream_t st);
-// plane nodes after the pass: open-plane rule at the next parity, exact density
-void push_plane(const DevState &s, unsigned long long *acc, int parity_next, cudaStream_t st);
-void push_wall(const DevState &s, unsigned long long *acc, cudaStream_t st);
+// After the pass: plane nodes (open-plane rule at the next parity, exact
+// density), the walls [w_lo, w_hi) and the clearing of clr in one launch,
+// then the other walls (those within two planes of an open plane).  Returns
+// the launch count.
+int push_finish(const DevState &s, unsigned long long *acc, unsigned long long *clr, int parity_next, int w_lo,
+                int w_hi, cudaStream_t st);
 // densities from the float psi of a density + wall pass (fluid and wall voxels)
 // (walls = false: fluid voxels only, as the brick schedule keeps them)
 void push_prime(const DevState &s, unsigned long long *acc, cudaStream_t st, bool walls = true);

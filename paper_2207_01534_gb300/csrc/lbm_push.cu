@@ -7,22 +7,26 @@ void push_fused(const DevState &s, const PushBufs &pb, int parity, cudaStream_t 
 {
     if (s.n_fluid == 0) return;
     const int g = (s.n_fluid + 255) / 256;
-    if (parity) k_fused_push<1><<<g, 256, 0, st>>>(s, pb);
-    else k_fused_push<0><<<g, 256, 0, st>>>(s, pb);
+    if (parity) launch_pdl(k_fused_push<1>, (unsigned)g, 256, 0, st, s, pb);
+    else launch_pdl(k_fused_push<0>, (unsigned)g, 256, 0, st, s, pb);
 }
 
-void push_plane(const DevState &s, unsigned long long *acc, int parity_next, cudaStream_t st)
+int push_finish(const DevState &s, unsigned long long *acc, unsigned long long *clr, int parity_next, int w_lo,
+                int w_hi, cudaStream_t st)
 {
-    if (!s.open_z || s.nxy == 0) return;
-    const int g = (2 * s.nxy + 127) / 128;
-    if (parity_next) k_plane_push<1><<<g, 128, 0, st>>>(s, acc);
-    else k_plane_push<0><<<g, 128, 0, st>>>(s, acc);
-}
-
-void push_wall(const DevState &s, unsigned long long *acc, cudaStream_t st)
-{
-    if (s.n_wall == 0) return;
-    k_wall_push<<<(s.n_wall + 255) / 256, 256, 0, st>>>(s, acc);
+    if (!s.open_z) w_lo = 0, w_hi = s.n_wall;
+    const int nbp = s.open_z ? (2 * s.nxy + 255) / 256 : 0;
+    const int nbw = (w_hi - w_lo + 255) / 256;
+    const int nbz = (int)(((s.nv + 1) / 2 + 255) / 256);
+    if (parity_next) launch_pdl(k_pw_push<1>, (unsigned)(nbp + nbw + nbz), 256, 0, st, s, acc, clr, nbp, nbw, w_lo, w_hi);
+    else launch_pdl(k_pw_push<0>, (unsigned)(nbp + nbw + nbz), 256, 0, st, s, acc, clr, nbp, nbw, w_lo, w_hi);
+    int launches = 1;
+    const int rest = w_lo + (s.n_wall - w_hi);
+    if (rest > 0) {
+        launch_pdl(k_wall_push, (unsigned)((rest + 255) / 256), 256, 0, st, s, acc, 0, w_lo, w_hi, s.n_wall);
+        ++launches;
+    }
+    return launches;
 }
 
 void push_prime(const DevState &s, unsigned long long *acc, cudaStream_t st, bool walls)

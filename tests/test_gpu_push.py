@@ -72,6 +72,23 @@ def test_open_drainage_porous(lbm, bc):
         _compare_rho(g, o, TOL_FP32_RHO)
 
 
+def test_open_drainage_walled_lateral_faces(lbm):
+    """Walled x and y faces reach the open planes, so some walls read plane
+    nodes (they are finished after them); the fluid rows end at walls, so
+    the warp-combined pushes see rows that end inside a warp."""
+    solid = inputs.add_lateral_walls(_open_porous((30, 18, 21), seed=5))
+    r1, r2 = inputs.drainage_init(solid, 4)
+    kw = dict(tau=inputs.tau_for_viscosity_ratio(10.0), G=3.5, xi=inputs.xi_of_theta(60.0), periodic=(0, 0, 0),
+              open_axis=2, rho_in1=1.08, rho_out2=1.0, bc="neem")
+    g, o = _pair(lbm, solid, **kw)
+    g.init_densities(r1, r2)
+    o.init_densities(r1, r2)
+    for chunk in (1, 2, 97, 200):
+        g.step(chunk)
+        o.step(chunk)
+        _compare_rho(g, o, TOL_FP32_RHO)
+
+
 def test_walls_body_force_and_ragged_size(lbm):
     solid = _porous_periodic((17, 23, 29), 9)
     r1, r2 = inputs.droplet_densities(solid.shape, (14, 11, 8), 5.0, 4.0, 1.0, 0.03)

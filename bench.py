@@ -169,7 +169,7 @@ class ClockSampler:
 # the files that define and instantiate the split passes (k_dens, k_wall,
 # k_fused) whose DRAM traffic profiles/traffic.json records
 TRAFFIC_SOURCES = ("lbm_internal.h", "lbm_kernels.cuh", "lbm_ops.inl", "lbm_fp32.cu", "lbm_fp64.cu", "lbm_fp16.cu",
-                   "lbm_bf16.cu")
+                   "lbm_bf16.cu", "lbm_fixed.cuh", "lbm_push.cuh", "lbm_push.cu")
 
 
 def kernel_source_hash():
@@ -310,6 +310,68 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def form_rate(lbm, solid, r1, r2, kw, nf, storage, kernel, steps, warmup=50):
+    """One storage form or schedule on the headline workload: MLUPS over
+    `steps` graph-replayed steps (CUDA events on the lattice's stream) and
+    the collide-stream pass's device time from event-timed steps."""
+    import torch
+
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        lat = lbm.Lattice(solid, kernel=kernel, storage=storage, stream=stream.cuda_stream, **kw)
+        lat.init_densities(r1, r2)
+        lat.step(warmup)
+        lat.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        lat.step(steps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        kms = lat.step_timed(200) / 200
+        lat.synchronize()
+        lat.close()
+    peak, _ = peaks()
+    algo = ALGO_BYTES[storage]
+    out = {"value": nf * steps / (ms / 1e3) / 1e6, "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+           "storage": storage, "kernel_schedule": kernel,
+           "step_frac": algo * nf / (ms / steps / 1e3) / 1e9 / peak}
+    if kms[2] > 0:
+        out["collide_stream_ms"] = float(kms[2])
+        out["collide_stream_frac"] = algo * nf / (float(kms[2]) / 1e3) / 1e9 / peak
+    return out
+
+
+def other_forms(args, lbm, solid, r1, r2, kw, nf, value, dist, local):
+    """The 16-bit storage forms, the push schedule, the batched sweep and the
+    adjoint, each measured after the headline FP32 number in the same run on
+    the same GPU and reported against it."""
+    forms = {"basis": "measured after the headline number, same run and GPU; each form on its own stream with "
+                      "inputs resident; ratios against the headline FP32 split-schedule value"}
+    for st in ("fp16dev", "bf16dev"):
+        f = form_rate(lbm, solid, r1, r2, kw, nf, st, "auto", 2000)
+        f["over_fp32"] = f["value"] / value
+        forms[st] = f
+    f = form_rate(lbm, solid, r1, r2, kw, nf, "fp32", "push", 2000)
+    f["over_split"] = f["value"] / value
+    forms["push"] = f
+    sub = argparse.Namespace(**vars(args))
+    sub.steps, sub.warmup, sub.storage = 100, 10, "fp32"
+    b = batch_line(sub, 1, dist, local)
+    forms["batch"] = {"workload": BATCH_WORKLOAD, "value": b["value"], "unit": UNIT, "steps": sub.steps,
+                      "samples": b["config"].get("samples", args.batch_count),
+                      "batch_over_solo": b["config"]["batch_over_solo"],
+                      "solo_sequential_mlups": b["config"]["solo_sequential_mlups"],
+                      "step_frac": b["roofline"]["frac"]}
+    a = adjoint_line(args, 1, dist, local)
+    forms["adjoint"] = {"workload": ADJOINT_WORKLOAD, "value": a["value"], "unit": UNIT, "steps": a["steps"],
+                        "adjoint_over_forward_time": a["config"]["adjoint_over_forward_time"],
+                        "forward_steps_per_s": a["config"]["forward_steps_per_s"],
+                        "roofline_frac": a["roofline"]["frac"],
+                        "algorithmic_bytes_per_node_step": ADJ_BYTES}
+    return forms
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -361,7 +423,8 @@ def run_ours(args, rank, world):
     achieved = algo * nf / (fused_ms / 1e3) / 1e9
     step_bytes_rate = algo * nf / (ms / args.steps / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": measured_traffic("k_fused", args.storage) if args.kernel in ("auto", "split") else None,
+            "traffic": measured_traffic({"auto": "k_fused", "split": "k_fused", "push": "k_fused_push"}.get(args.kernel),
+                                        args.storage),
             "kernel": {"brick": "k_brick", "push": "k_fused_push", "fused": "k_pipe", "flow": "k_flow"}.get(args.kernel,
                                                                                                          "k_fused"),
             "peak_kind": peak_kind,
@@ -413,20 +476,31 @@ def run_ours(args, rank, world):
             "vs_baseline": None, "dtype": DTYPE[args.storage], "data": "synthetic", "config": cfg, "roofline": roof,
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
             "saturation": {"S_w": sat[0], "S_nw_smooth": sat[1]}}
+    if world == 1 and not args.no_forms and args.kernel == "auto" and args.storage == "fp32":
+        line["forms"] = other_forms(args, lbm, solid, r1, r2, kw, nf, value, dist, local)
     if rank == 0:
         print(json.dumps(line), flush=True)
     dist_finish(dist)
 
 
 def run_batch(args, rank, world):
-    import tempfile
-
-    samples, states, cfg = batch_setup(args.batch_count, tuple(args.batch_edges))
     import torch
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = dist_init(world)
+    line = batch_line(args, world, dist, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist_finish(dist)
+
+
+def batch_line(args, world, dist, local):
+    import tempfile
+
+    samples, states, cfg = batch_setup(args.batch_count, tuple(args.batch_edges))
+    import torch
+
     from paper_2207_01534_gb300 import lbm
 
     lbm.load()
@@ -509,20 +583,27 @@ def run_batch(args, rank, world):
             "cpu_baseline": None, "gpu_launches": int(launches), "clocks": clk,
             "e2e": {"value": nf * args.steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
                     "d2h_bytes_per_step": d2h / args.steps}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    dist_finish(dist)
+    return line
 
 
 def run_adjoint(args, rank, world):
     import torch
 
-    from paper_2207_01534_gb300 import inputs
-
-    solid, r1, r2 = inputs.adjoint_pack_96()
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dist = dist_init(world)
+    line = adjoint_line(args, world, dist, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist_finish(dist)
+
+
+def adjoint_line(args, world, dist, local):
+    import torch
+
+    from paper_2207_01534_gb300 import inputs
+
+    solid, r1, r2 = inputs.adjoint_pack_96()
     from paper_2207_01534_gb300 import lbm
 
     lbm.load()
@@ -587,9 +668,7 @@ def run_adjoint(args, rank, world):
                          "algorithmic_bytes_per_node_step": ADJ_BYTES,
                          "bytes_basis": "record 308 (a forward step) + recompute 304 + segment state stored and "
                                         "read 304 + adjoint populations read and written 304 + voxel index 4"}}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    dist_finish(dist)
+    return line
 
 
 def main():
@@ -604,6 +683,7 @@ def main():
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp64", "fp16dev", "bf16dev"))
     ap.add_argument("--cpu-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the 16-bit, push, batch and adjoint forms")
     ap.add_argument("--workload", default=WORKLOAD, choices=(WORKLOAD, BATCH_WORKLOAD, ADJOINT_WORKLOAD))
     ap.add_argument("--tune-cache", default=None, help="autotuner JSON cache (batched workload)")
     ap.add_argument("--batch-count", type=int, default=64, help="samples (batched workload)")

@@ -638,13 +638,6 @@ __device__ __forceinline__ void dens_node_at(int n, const DevState &s, int neem)
     dens_node_geo<TS, P>(n, s.pvox[n], s.nflags[n], s, neem);
 }
 
-template <typename TS, int P>
-__device__ __forceinline__ void dens_pass_node(int t, const DevState &s, int neem)
-{
-    if (t >= s.n_fluid) return;
-    dens_node_at<TS, P>(s.n_fluid - 1 - t, s, neem);
-}
-
 // Resident blocks per SM of the density pass: four for FP32 and 16-bit
 // storage (the odd-parity gather otherwise takes 80 registers and three
 // blocks: 39.7 vs 36.8 us per pass on the 128^3 pack), two for FP64.
@@ -916,9 +909,10 @@ __global__ void __launch_bounds__(256) k_dens_batch(const DevState *states, cons
     pdl_trigger();
     pdl_wait();
     __shared__ __align__(16) DevState sh;
-    const int2 m = map[blockIdx.x];
+    const int2 m = map[gridDim.x - 1 - blockIdx.x];  // last node of the last sample first, as k_dens_table
     const DevState &s = stage_state(states, m.x, &sh);
-    dens_pass_node<TS, P>(m.y * blockDim.x + threadIdx.x, s, neem && s.open_z);
+    const int n = m.y * blockDim.x + threadIdx.x;
+    if (n < s.n_fluid) dens_node_at<TS, P>(n, s, neem && s.open_z);
 }
 
 template <typename TS>
@@ -949,26 +943,33 @@ __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused_batch(const 
 // block's sample is the last k with start[k] <= blockIdx.x (binary search in
 // parameter memory), its node or wall index the rest; the geometry words are
 // read before the dependent-launch wait, as in the solo passes.
-__device__ __forceinline__ int table_sample(const int *start, int count)
+__device__ __forceinline__ int table_sample(const int *start, int count, int blk)
 {
-    int lo = 0, hi = count - 1;  // start[lo] <= blockIdx.x < start[hi + 1]
+    int lo = 0, hi = count - 1;  // start[lo] <= blk < start[hi + 1]
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (start[mid] <= (int)blockIdx.x) lo = mid;
+        if (start[mid] <= blk) lo = mid;
         else hi = mid - 1;
     }
     return lo;
+}
+__device__ __forceinline__ int table_sample(const int *start, int count)
+{
+    return table_sample(start, count, (int)blockIdx.x);
 }
 
 template <typename TS, int P>
 __global__ void __launch_bounds__(256, DensOcc<TS>::blocks) k_dens_table(const __grid_constant__ BatchTable t, int neem)
 {
     pdl_trigger();
-    const int k = table_sample(t.start_n, t.count);
+    // the whole batch last node first (samples in reverse order too), so the
+    // pass starts on the cells the collide-stream pass wrote last and ends on
+    // those its next launch reads first
+    const int rb = t.start_n[t.count] - 1 - (int)blockIdx.x;
+    const int k = table_sample(t.start_n, t.count, rb);
     const DevState &s = t.s[k];
-    const int q = ((int)blockIdx.x - t.start_n[k]) * (int)blockDim.x + (int)threadIdx.x;
-    const bool live = q < s.n_fluid;
-    const int n = s.n_fluid - 1 - q;
+    const int n = (rb - t.start_n[k]) * (int)blockDim.x + (int)threadIdx.x;
+    const bool live = n < s.n_fluid;
     const uint32_t pv = live ? s.pvox[n] : 0u;
     const uint32_t fl = live ? s.nflags[n] : 0u;
     pdl_wait();

@@ -424,9 +424,12 @@ __device__ __forceinline__ C2 sum19(const C2 f[19])
 // density is then density_of(dm) = rho_ref + dm.  LD selects the load mode
 // (LD_CG for data other blocks of the launch wrote, LD_CA for data this
 // thread wrote).
-template <typename TS, int P, int LD = LD_NC>
+// kRec (parity 1 only): also write each in-block slot offset to rec[(j-1)*rs],
+// so that store_pops can take it back instead of looking the partner up again.
+template <typename TS, int P, int LD = LD_NC, bool kRec = false>
 __device__ __forceinline__ void load_pops(typename Traits<TS>::C2 f[19], typename Traits<TS>::C2 &dm, int n,
-                                          uint32_t pv, uint32_t fl, const Nbr &b, const DevState &s)
+                                          uint32_t pv, uint32_t fl, const Nbr &b, const DevState &s,
+                                          unsigned *rec = nullptr, int rs = 0)
 {
     using C2 = typename Traits<TS>::C2;
     using S2 = typename Traits<TS>::S2;
@@ -442,8 +445,14 @@ __device__ __forceinline__ void load_pops(typename Traits<TS>::C2 f[19], typenam
     }
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
-        const S2 *p = (ez(j) != 0 && plane && outside(j, fl)) ? B + bc_cell(j, pv, fl, s)
-                                                               : M + slot_in_block<P>(j, n, pv, b, s);
+        const S2 *p;
+        if (ez(j) != 0 && plane && outside(j, fl)) {
+            p = B + bc_cell(j, pv, fl, s);
+        } else {
+            const unsigned o = slot_in_block<P>(j, n, pv, b, s);
+            if constexpr (kRec) rec[(j - 1) * rs] = o;
+            p = M + o;
+        }
         if constexpr (Traits<TS>::kDev) {
             const C2 d = Traits<TS>::template load_dev<LD>(p);
             dm = add2(dm, d);
@@ -463,9 +472,10 @@ __device__ __forceinline__ void load_pops(typename Traits<TS>::C2 f[19], typenam
 // (never re-quantised).  kBack: f[] receives the stored values back (the
 // dequantised codes and the stored rest population), as a later load would
 // return them.
-template <typename TS, int P, bool kBack = false>
+template <typename TS, int P, bool kBack = false, bool kRec = false>
 __device__ __forceinline__ void store_pops(typename Traits<TS>::C2 f[19], typename Traits<TS>::C2 dm, int n,
-                                           uint32_t pv, uint32_t fl, const Nbr &b, const DevState &s)
+                                           uint32_t pv, uint32_t fl, const Nbr &b, const DevState &s,
+                                           const unsigned *rec = nullptr, int rs = 0)
 {
     using C2 = typename Traits<TS>::C2;
     using S2 = typename Traits<TS>::S2;
@@ -490,7 +500,8 @@ __device__ __forceinline__ void store_pops(typename Traits<TS>::C2 f[19], typena
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
         if (ez(j) != 0 && plane && outside(j, fl)) continue;  // leaves the domain
-        Traits<TS>::store_q(M + slot_in_block<P>(j, n, pv, b, s), q[j]);
+        const unsigned o = kRec ? rec[(j - 1) * rs] : slot_in_block<P>(j, n, pv, b, s);
+        Traits<TS>::store_q(M + o, q[j]);
     }
 }
 
@@ -720,21 +731,32 @@ __global__ void __launch_bounds__(256) k_wall(DevState s, int w0, int w1)
 // in the same order), so the force stencil runs before the populations are
 // loaded and the stencil's and the populations' loads never hold registers
 // at the same time.
-template <typename TS, int P>
-__device__ __forceinline__ void fused_node_geo(int n, uint32_t pv, uint32_t fl, const DevState &s)
+// At parity 1 with rec != nullptr, the 18 slot offsets found at the load
+// are kept in shared memory (rec[(j-1) * rs], this thread's column) and
+// reused for the stores, which then wait on no index loads.
+template <typename TS, int P, bool kRec = false>
+__device__ __forceinline__ void fused_node_geo(int n, uint32_t pv, uint32_t fl, const DevState &s,
+                                               unsigned *rec = nullptr, int rs = 0)
 {
     using C = typename Traits<TS>::C;
     using C2 = typename Traits<TS>::C2;
+    constexpr bool R = kRec && P == 1;
     const Nbr b = make_nbr(fl, s);
     const C2 rho = ld_pol(reinterpret_cast<const C2 *>(s.psi) + pv, l2_policy());
     C2 F[3];
     forces<TS>(rho, pv, fl, b, s, F);
     C2 f[19], dm;
-    load_pops<TS, P>(f, dm, n, pv, fl, b, s);
+    load_pops<TS, P, LD_NC, R>(f, dm, n, pv, fl, b, s, rec, rs);
     C u[3], inv_rho;
     mix_velocity<C, C2>(f, rho, F, s, inv_rho, u);
     collide<C, C2>(f, rho, inv_rho, u, F, s);
-    store_pops<TS, P>(f, dm, n, pv, fl, b, s);
+    store_pops<TS, P, false, R>(f, dm, n, pv, fl, b, s, rec, rs);
+}
+
+// Shared memory of the collide-stream kernels at parity 1: 18 slot offsets per thread.
+__host__ __device__ constexpr size_t slot_rec_bytes(int parity, int block)
+{
+    return parity ? (size_t)18 * sizeof(unsigned) * (size_t)block : 0;
 }
 
 template <typename TS, int P>
@@ -744,9 +766,11 @@ __device__ __forceinline__ void fused_node(int n, const DevState &s)
 }
 
 // nodes [n0, n1); the node's voxel and flags are read before the wait
-template <typename TS, int P>
+// kRec: parity-1 slot offsets kept in dynamic shared memory (slot_rec_bytes)
+template <typename TS, int P, bool kRec = false>
 __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused(DevState s, int n0, int n1)
 {
+    extern __shared__ unsigned slot_rec[];
     pdl_trigger();
     const int n = n0 + (int)(blockIdx.x * blockDim.x + threadIdx.x);
     const bool live = n < n1;
@@ -754,7 +778,7 @@ __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused(DevState s, 
     const uint32_t fl = live ? s.nflags[n] : 0u;
     pdl_wait();
     if (!live) return;
-    fused_node_geo<TS, P>(n, pv, fl, s);
+    fused_node_geo<TS, P, kRec>(n, pv, fl, s, slot_rec + threadIdx.x, (int)blockDim.x);
 }
 
 // Open planes, for the parity PN of the step that reads next: the prescribed
@@ -997,6 +1021,7 @@ __global__ void __launch_bounds__(256) k_wall_table(const __grid_constant__ Batc
 template <typename TS, int P>
 __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused_table(const __grid_constant__ BatchTable t)
 {
+    extern __shared__ unsigned slot_rec[];  // parity 1: slot_rec_bytes(1, blockDim.x)
     pdl_trigger();
     const int k = table_sample(t.start_n, t.count);
     const DevState &s = t.s[k];
@@ -1006,7 +1031,7 @@ __global__ void __launch_bounds__(256, PipeOcc<TS>::blocks) k_fused_table(const 
     const uint32_t fl = live ? s.nflags[n] : 0u;
     pdl_wait();
     if (!live) return;
-    fused_node_geo<TS, P>(n, pv, fl, s);
+    fused_node_geo<TS, P, true>(n, pv, fl, s, slot_rec + threadIdx.x, (int)blockDim.x);
 }
 
 // ---------------------------------------------------------------------------

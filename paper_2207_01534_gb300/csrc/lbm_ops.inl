@@ -13,8 +13,8 @@ void Ops<TS>::dens(const DevState &s, int parity, int neem, cudaStream_t st, int
 {
     if (n1 < 0) n1 = s.n_fluid;
     if (n1 <= n0) return;
-    const unsigned g = grid_for(n1 - n0, block);
     const int ne = neem && s.open_z;
+    const unsigned g = grid_for(n1 - n0, block);
     if (parity) launch_pdl(k_dens<TS, 1>, g, block, 0, st, s, ne, n0, n1);
     else launch_pdl(k_dens<TS, 0>, g, block, 0, st, s, ne, n0, n1);
 }
@@ -33,7 +33,9 @@ void Ops<TS>::fused(const DevState &s, int parity, cudaStream_t st, int block, i
     if (n1 < 0) n1 = s.n_fluid;
     if (n1 <= n0) return;
     const unsigned g = grid_for(n1 - n0, block);
-    if (parity) launch_pdl(k_fused<TS, 1>, g, block, 0, st, s, n0, n1);
+    // parity 1 keeps its slot offsets in shared memory between the loads and
+    // the stores (128^3 pack: FP32 50.0 -> 48.7 us, FP16 43.0 -> 40.4 us)
+    if (parity) launch_pdl(k_fused<TS, 1, true>, g, block, slot_rec_bytes(1, block), st, s, n0, n1);
     else launch_pdl(k_fused<TS, 0>, g, block, 0, st, s, n0, n1);
 }
 
@@ -83,7 +85,7 @@ void Ops<TS>::fused_table(const BatchTable &t, int parity, cudaStream_t st, int 
 {
     const int nb = t.start_n[t.count];
     if (nb <= 0) return;
-    if (parity) launch_pdl(k_fused_table<TS, 1>, (unsigned)nb, block, 0, st, t);
+    if (parity) launch_pdl(k_fused_table<TS, 1>, (unsigned)nb, block, slot_rec_bytes(1, block), st, t);
     else launch_pdl(k_fused_table<TS, 0>, (unsigned)nb, block, 0, st, t);
 }
 

@@ -508,7 +508,8 @@ def batch_line(args, world, dist, local):
     stream = torch.cuda.Stream()
     cache = args.tune_cache or os.path.join(tempfile.gettempdir(), "lbm_autotune.json")
     with torch.cuda.stream(stream):
-        b = lbm.Batch([dict(kw, storage=args.storage) for kw in samples], stream=stream.cuda_stream)
+        bkern = "persistent" if args.kernel == "persistent" else "split"
+        b = lbm.Batch([dict(kw, storage=args.storage, kernel=bkern) for kw in samples], stream=stream.cuda_stream)
         for smp, (r1, r2) in zip(b.samples, states):
             smp.init_densities(r1, r2)
         b.step(args.warmup)
@@ -571,11 +572,13 @@ def batch_line(args, world, dist, local):
     algo = ALGO_BYTES[args.storage]
     achieved = algo * nf / (ms / args.steps / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "kernel": "whole batched step (k_dens_batch + k_wall_batch + k_fused_batch)",
+            "traffic": None,
+            "kernel": ("whole batched step (k_persist: all steps of a launch, grid barriers between the passes)"
+                       if bkern == "persistent" else "whole batched step (k_dens_table + k_wall_table + k_fused_table)"),
             "peak_kind": peak_kind, "algorithmic_bytes_per_node": algo}
     cfg = dict(cfg)
     cfg.update({"parallelism": "replicas" if world > 1 else "single", "storage": args.storage, "block": block,
-                "solo_sequential_mlups": nf * args.steps / (ms_solo / 1e3) / 1e6,
+                "batch_schedule": bkern, "solo_sequential_mlups": nf * args.steps / (ms_solo / 1e3) / 1e6,
                 "batch_over_solo": ms_solo / ms})
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -679,7 +682,8 @@ def main():
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--warmup", type=int, default=50)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--kernel", default="auto", choices=("auto", "split", "flow", "fused", "wave", "push", "brick"))
+    ap.add_argument("--kernel", default="auto",
+                    choices=("auto", "split", "flow", "fused", "wave", "push", "brick", "persistent"))
     ap.add_argument("--storage", default="fp32", choices=("fp32", "fp64", "fp16dev", "bf16dev"))
     ap.add_argument("--cpu-steps", type=int, default=60)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -62,7 +62,8 @@ enum {
     LBM_KERNEL_WAVE = 3,  /* the split passes per z slab, as a dependency graph (see lbm_step) */
     LBM_KERNEL_PUSH = 4,  /* collide-stream pass that also accumulates the next densities (FP32; see lbm_step) */
     LBM_KERNEL_BRICK = 5, /* one pass per step over 8^3 bricks, halo densities in shared memory (see lbm_step) */
-    LBM_KERNEL_FLOW = 6   /* one launch per step: collide-stream, then next densities from L2 (see lbm_step) */
+    LBM_KERNEL_FLOW = 6,  /* one launch per step: collide-stream, then next densities from L2 (see lbm_step) */
+    LBM_KERNEL_PERSISTENT = 7 /* batches: many steps of all samples in one cooperative launch (see lbm_step) */
 };
 
 /* Open-plane rule for the prescribed component (Section 2, boundary rule 1):
@@ -227,6 +228,18 @@ lbm_status lbm_create_batch(int32_t n, const lbm_geometry *geoms, const lbm_para
 int32_t lbm_batch_size(const lbm_ctx *batch);
 lbm_status lbm_batch_get(lbm_ctx *batch, int32_t k, lbm_ctx **sample);
 
+/* LBM_KERNEL_PERSISTENT (batches of up to 96 samples; params[0].kernel of
+ * lbm_create_batch; LBM_ERR_UNSUPPORTED for a single lattice or a larger
+ * batch): lbm_step runs up to 256 steps of every sample in one cooperative
+ * launch whose blocks are all resident.  Each step is the split schedule's
+ * three passes over all samples (densities with the open-plane rule, virtual
+ * wall densities, force + collision + streaming), separated by grid-wide
+ * barriers; the blocks deal the batch's node and wall blocks among themselves
+ * with the same per-node arithmetic as the batched passes, so every sample's
+ * results are bitwise those of its solo run.  Each barrier wait is bounded
+ * (lbm_set_wait_limit, default 1 s); see Failure handling.  reduce_every > 0
+ * on any sample steps the batch with the three-launch passes instead. */
+
 /* lbm_step on a single lattice or a batch with the split schedule (or a
  * single lattice with the flow schedule), reduce_every = 0 and n >= 4 replays
  * steps from two CUDA graphs, captured
@@ -328,8 +341,9 @@ lbm_status lbm_record(lbm_ctx *ctx, int64_t nsteps, int32_t every);
 lbm_status lbm_adjoint(lbm_ctx *ctx, double dloss, float *grad_xi, double *grad_rho_in1, double *loss);
 
 /* ---- Failure handling ----------------------------------------------------
- * The single-pass and flow schedules (LBM_KERNEL_FUSED, LBM_KERNEL_FLOW)
- * order their blocks with device waits; each wait gives up after a time limit (default 1 s, measured with the
+ * The single-pass and flow schedules (LBM_KERNEL_FUSED, LBM_KERNEL_FLOW) and
+ * the persistent batch launch (LBM_KERNEL_PERSISTENT) order their blocks with
+ * device waits; each wait gives up after a time limit (default 1 s, measured with the
  * GPU's global timer), sets an abort word that stops every block, and raises
  * LBM_ERR_TIMEOUT from the next lbm_step / lbm_synchronize.  The kernel then
  * returns normally: the context stays usable, the populations of the
@@ -340,8 +354,11 @@ lbm_status lbm_adjoint(lbm_ctx *ctx, double dloss, float *grad_xi, double *grad_
  * lbm_set_wait_limit sets the limit (0 < seconds <= 60).  lbm_inject_stall
  * makes the next single-pass step wait for a round that never completes (the
  * next flow step: one density item waits for a flag value that is never
- * written), so that the timeout path can be tested without faulting or
- * hanging the GPU (LBM_ERR_UNSUPPORTED for other schedules). */
+ * written; the next persistent launch: one block never reaches its first
+ * grid barrier), so that the timeout path can be tested without faulting or
+ * hanging the GPU (LBM_ERR_UNSUPPORTED for other schedules).  For a batch,
+ * re-initialising a sample (lbm_init_densities, lbm_set_populations) clears
+ * the batch's timeout record. */
 lbm_status lbm_set_wait_limit(lbm_ctx *ctx, double seconds);
 lbm_status lbm_inject_stall(lbm_ctx *ctx);
 

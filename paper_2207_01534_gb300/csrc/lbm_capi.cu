@@ -88,6 +88,10 @@ struct lbm_ctx {
     int n_map_n = 0, n_map_w = 0, map_block = 0;
     BatchTable *table = nullptr;  // batches of up to kParamStates samples: states and block offsets
     bool states_dirty = true;
+    // persistent batch launch (LBM_KERNEL_PERSISTENT): grid-barrier counter
+    // and abort word, both cleared before every launch
+    unsigned long long *d_bar = nullptr;
+    int *d_abort = nullptr;
     // CUDA graph of two split-schedule steps, captured on a private stream
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -459,6 +463,9 @@ lbm_status capture_initial_mass(lbm_ctx *c)
     c->mass0[0] = red[0];
     c->mass0[1] = red[1];
     if (c->h_flag) *c->h_flag = 0;
+    // a new state of a sample also clears its batch's record of an abandoned
+    // persistent launch (the sample's batch starts over from here)
+    if (c->parent && c->parent->h_flag) *c->parent->h_flag = 0;
     return LBM_OK;
 }
 
@@ -1388,6 +1395,8 @@ lbm_status lbm_create(const lbm_geometry *g, const lbm_params *p, lbm_ctx **out)
     if (!(p->tau[0] > 0.5) || !(p->tau[1] > 0.5)) return fail(nullptr, LBM_ERR_ARG, "tau must exceed 1/2");
     if (p->bc != LBM_BC_NEEM && p->bc != LBM_BC_ZOU_HE) return fail(nullptr, LBM_ERR_UNSUPPORTED, "unknown open-plane rule");
     if (p->reduce_every < 0) return fail(nullptr, LBM_ERR_ARG, "reduce_every must be >= 0");
+    if (p->kernel == LBM_KERNEL_PERSISTENT)
+        return fail(nullptr, LBM_ERR_UNSUPPORTED, "the persistent launch steps batches (lbm_create_batch)");
 
     const int per[3] = {g->periodic[0] ? 1 : 0, g->periodic[1] ? 1 : 0, g->periodic[2] ? 1 : 0};
     const int dims[3] = {nx, ny, nz};
@@ -2106,6 +2115,50 @@ lbm_status lbm_get_populations(lbm_ctx *c, double *f)
     return st != LBM_OK ? st : device_status(c);
 }
 
+// A batch's steps in persistent cooperative launches of up to kPersistSteps
+// steps each (lbm_persist.cuh).
+constexpr int kPersistSteps = 256;
+
+lbm_status step_persistent(lbm_ctx *c, int64_t n)
+{
+    cudaStream_t st = c->stream;
+    c->pipe_reset = false;
+    const int nbn = c->table->start_n[c->table->count], nbw = c->table->start_w[c->table->count];
+    int grid = 0;
+    dispatch(c, [&](auto tag) { grid = Ops<decltype(tag)>::persist_grid(c->map_block); });
+    grid = std::min(grid, std::max(1, std::max(nbn, nbw)));
+    if (grid <= 0) return fail(c, LBM_ERR_CUDA, "the persistent launch does not fit on this device");
+    for (int64_t k = 0; k < n;) {
+        const int steps = (int)std::min<int64_t>(kPersistSteps, n - k);
+        // every launch starts its barrier count and abort word from zero (a
+        // launch that gave up leaves its count short)
+        cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned long long), st);
+        cudaMemsetAsync(c->d_abort, 0, sizeof(int), st);
+        PersistArgs pa{};
+        pa.bar = c->d_bar;
+        pa.abort = c->d_abort;
+        pa.status = c->d_flag;
+        pa.base = 0;
+        pa.wait_ns = c->ps.wait_ns;
+        pa.step0 = cur_step(c);
+        pa.steps = steps;
+        pa.stall = c->stall_next ? 1 : 0;
+        c->stall_next = false;
+        cudaError_t e = cudaSuccess;
+        dispatch(c, [&](auto tag) { e = Ops<decltype(tag)>::persist(*c->table, pa, grid, c->map_block, st); });
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return cuda_fail(c, e, "persistent launch");
+        }
+        for (lbm_ctx *q : c->subs) q->step += steps;
+        c->step += steps;
+        c->launches += 1;
+        k += steps;
+    }
+    lbm_status stt = check_launch(c, "lbm_step");
+    return stt != LBM_OK ? stt : device_status(c);
+}
+
 lbm_status lbm_step(lbm_ctx *c, int64_t n)
 {
     if (!c || n < 0) return LBM_ERR_ARG;
@@ -2119,6 +2172,7 @@ lbm_status lbm_step(lbm_ctx *c, int64_t n)
             if (st != LBM_OK) return st;
         }
     }
+    if (c->kernel == LBM_KERNEL_PERSISTENT && !any_reduce(c) && n > 0) return step_persistent(c, n);
     int64_t k = 0;
     if (acc_schedule(c) && n > 0) push_prime_ctx(c);
     const int align = acc_schedule(c) ? 6 : 2;
@@ -2169,7 +2223,7 @@ lbm_status lbm_create_batch(int32_t n, const lbm_geometry *geoms, const lbm_para
     for (int32_t k = 0; k < n; ++k) {
         lbm_params pk = params[k];
         if (pk.kernel == LBM_KERNEL_FUSED || pk.kernel == LBM_KERNEL_BRICK || pk.kernel == LBM_KERNEL_FLOW ||
-            pk.kernel == LBM_KERNEL_AUTO)
+            pk.kernel == LBM_KERNEL_AUTO || pk.kernel == LBM_KERNEL_PERSISTENT)
             pk.kernel = LBM_KERNEL_SPLIT;
         lbm_ctx *q = nullptr;
         lbm_status st = lbm_create(&geoms[k], &pk, &q);
@@ -2203,6 +2257,29 @@ lbm_status lbm_create_batch(int32_t n, const lbm_geometry *geoms, const lbm_para
         g_create_err = c->err;
         destroy_ctx(c);
         return LBM_ERR_ALLOC;
+    }
+    if (params[0].kernel == LBM_KERNEL_PERSISTENT) {
+        if (n > kParamStates) {
+            destroy_ctx(c);
+            return fail(nullptr, LBM_ERR_UNSUPPORTED,
+                        "the persistent launch takes at most " + std::to_string(kParamStates) + " samples");
+        }
+        c->kernel = LBM_KERNEL_PERSISTENT;
+        c->ps.wait_ns = 1000000000ull;  // one second
+        c->d_bar = (unsigned long long *)dalloc(c, sizeof(unsigned long long));
+        c->d_abort = (int *)dalloc(c, sizeof(int));
+        cudaError_t e = c->d_bar && c->d_abort ? cudaSuccess : cudaErrorMemoryAllocation;
+        if (e == cudaSuccess) e = cudaMemset(c->d_bar, 0, sizeof(unsigned long long));
+        if (e == cudaSuccess) e = cudaMemset(c->d_abort, 0, sizeof(int));
+        if (e == cudaSuccess) e = cudaHostAlloc((void **)&c->h_flag, sizeof(int), cudaHostAllocMapped);
+        if (e == cudaSuccess) {
+            *c->h_flag = 0;
+            e = cudaHostGetDevicePointer((void **)&c->d_flag, c->h_flag, 0);
+        }
+        if (e != cudaSuccess) {
+            destroy_ctx(c);
+            return fail(nullptr, LBM_ERR_ALLOC, "persistent launch counters");
+        }
     }
     *out = c;
     return LBM_OK;
@@ -2638,8 +2715,9 @@ lbm_status lbm_set_wait_limit(lbm_ctx *c, double seconds)
 lbm_status lbm_inject_stall(lbm_ctx *c)
 {
     if (!c) return LBM_ERR_ARG;
-    if (c->kernel != LBM_KERNEL_FUSED && !(c->kernel == LBM_KERNEL_FLOW && c->flow_stall_slot >= 0))
-        return fail(c, LBM_ERR_UNSUPPORTED, "only the single-pass and flow schedules have device waits");
+    if (c->kernel != LBM_KERNEL_FUSED && c->kernel != LBM_KERNEL_PERSISTENT &&
+        !(c->kernel == LBM_KERNEL_FLOW && c->flow_stall_slot >= 0))
+        return fail(c, LBM_ERR_UNSUPPORTED, "only the single-pass, flow and persistent schedules have device waits");
     c->stall_next = true;
     return LBM_OK;
 }

@@ -157,6 +157,21 @@ struct BatchTable {
     int count;
 };
 
+// Persistent batch launch (lbm_persist.cuh): `steps` time steps of every
+// sample of a batch table in one cooperative launch, the passes separated by
+// grid barriers on a counter that only grows during the launch.
+struct PersistArgs {
+    unsigned long long *bar;     // grid barrier counter (cleared before the launch)
+    int *abort;                  // set by a block that gave up
+    int *status;                 // host-mapped status word (bit value 4: timeout)
+    unsigned long long base;     // counter value when the launch starts (0)
+    unsigned long long wait_ns;  // a barrier wait gives up after this long
+    long long step0;             // step of the batch when the launch starts
+    int steps;                   // time steps of this launch
+    int stall;                   // failure test: block 0 never arrives at the first barrier
+};
+static_assert(sizeof(BatchTable) + sizeof(PersistArgs) <= 32764, "kernel parameters of the persistent launch");
+
 // Per-storage-type kernel launchers, explicitly instantiated in one
 // translation unit per storage type.
 template <typename TS>
@@ -178,6 +193,11 @@ struct Ops {
     static void dens_table(const BatchTable &t, int parity, int neem, cudaStream_t st, int block);
     static void wall_table(const BatchTable &t, cudaStream_t st, int block);
     static void fused_table(const BatchTable &t, int parity, cudaStream_t st, int block);
+    // pa.steps steps of the whole table in one cooperative launch of `grid`
+    // blocks of `block` threads (block = the table's block size)
+    static cudaError_t persist(const BatchTable &t, const PersistArgs &pa, int grid, int block, cudaStream_t st);
+    // resident blocks of `block` threads on the current device for persist()
+    static int persist_grid(int block);
     static void plane(const DevState &s, int parity_next, cudaStream_t st);
     // rest equilibrium from device densities rho[2][nv] (double); parity-0 layout
     static void init_eq(const DevState &s, const double *rho, cudaStream_t st);

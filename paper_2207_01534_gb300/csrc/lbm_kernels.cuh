@@ -165,6 +165,22 @@ __device__ __forceinline__ float2 ld_pol(const float2 *q, unsigned long long pol
     return v;
 }
 __device__ __forceinline__ double2 ld_pol(const double2 *q, unsigned long long) { return __ldg(q); }
+// The same density-map loads for data written earlier in the same launch
+// (persistent kernels): ordinary coherent loads, which the compiler orders
+// against the launch's barriers like any other memory access.
+template <typename C2>
+__device__ __forceinline__ C2 ld_pol_coh(const C2 *q, unsigned long long)
+{
+    return *q;
+}
+// density-map load in mode LD: LD_NC read-only (data of earlier launches),
+// otherwise coherent
+template <int LD, typename C2>
+__device__ __forceinline__ C2 ld_psi(const C2 *q, unsigned long long pol)
+{
+    if constexpr (LD == LD_NC) return ld_pol(q, pol);
+    else return ld_pol_coh(q, pol);
+}
 
 // ---------------------------------------------------------------------------
 // Storage traits: how population pairs are kept in memory.  C / C2 are the
@@ -511,7 +527,7 @@ __device__ __forceinline__ void store_pops(typename Traits<TS>::C2 f[19], typena
 // mirrored direction's neighbour is used (Section 2).  The stencil sums
 // neighbour minus own value (the same sum, since sum_i w_i e_i = 0, with far
 // less cancellation error in FP32).
-template <typename TS>
+template <typename TS, int LD = LD_NC>
 __device__ __forceinline__ void forces(typename Traits<TS>::C2 rho, uint32_t pv, uint32_t fl, const Nbr &b,
                                        const DevState &s, typename Traits<TS>::C2 F[3])
 {
@@ -522,7 +538,7 @@ __device__ __forceinline__ void forces(typename Traits<TS>::C2 rho, uint32_t pv,
 #pragma unroll
     for (int j = 1; j < 19; ++j) {
         const int off = (ez(j) != 0 && outside(j, fl)) ? nb_off(mirz(j), b) : nb_off(j, b);
-        const C2 d = sub2(ld_pol(psi + off, l2_policy()), rho);
+        const C2 d = sub2(ld_psi<LD>(psi + off, l2_policy()), rho);
         const C w = wgt<C>(j);
         if (ex(j)) a[0] = fma2(bc2<C2>(w * ex(j)), d, a[0]);
         if (ey(j)) a[1] = fma2(bc2<C2>(w * ey(j)), d, a[1]);
@@ -628,14 +644,14 @@ __device__ __forceinline__ void neem_node(int plane, int p, int nb, uint32_t pvb
 // plane node reads back cells it has just written (read-only cache loads may
 // be ordered before those writes), and one shared load path keeps the
 // common case as lean as before.
-template <typename TS, int P>
+template <typename TS, int P, int LDI = LD_NC>
 __device__ __forceinline__ void dens_node_geo(int n, uint32_t pv, uint32_t fl, const DevState &s, int neem)
 {
     using C2 = typename Traits<TS>::C2;
     if (neem && (fl & (F_INLET | F_OUTLET))) {
         const int plane = (fl & F_INLET) ? 0 : 1;
         const int p = plane == 0 ? (int)pv : (int)pv - (s.nz - 1) * s.sxy;
-        neem_node<TS, P, LD_NC>(plane, p, n, pv, fl, s);
+        neem_node<TS, P, LDI>(plane, p, n, pv, fl, s);  // LDI: how it reads the interior node
     }
     const Nbr b = make_nbr(fl, s);
     C2 f[19], dm;
@@ -734,7 +750,9 @@ __global__ void __launch_bounds__(256) k_wall(DevState s, int w0, int w1)
 // At parity 1 with rec != nullptr, the 18 slot offsets found at the load
 // are kept in shared memory (rec[(j-1) * rs], this thread's column) and
 // reused for the stores, which then wait on no index loads.
-template <typename TS, int P, bool kRec = false>
+// LD: LD_NC when the populations and densities were written by earlier
+// launches, LD_CA inside a persistent launch that wrote them itself.
+template <typename TS, int P, bool kRec = false, int LD = LD_NC>
 __device__ __forceinline__ void fused_node_geo(int n, uint32_t pv, uint32_t fl, const DevState &s,
                                                unsigned *rec = nullptr, int rs = 0)
 {
@@ -742,11 +760,11 @@ __device__ __forceinline__ void fused_node_geo(int n, uint32_t pv, uint32_t fl, 
     using C2 = typename Traits<TS>::C2;
     constexpr bool R = kRec && P == 1;
     const Nbr b = make_nbr(fl, s);
-    const C2 rho = ld_pol(reinterpret_cast<const C2 *>(s.psi) + pv, l2_policy());
+    const C2 rho = ld_psi<LD>(reinterpret_cast<const C2 *>(s.psi) + pv, l2_policy());
     C2 F[3];
-    forces<TS>(rho, pv, fl, b, s, F);
+    forces<TS, LD>(rho, pv, fl, b, s, F);
     C2 f[19], dm;
-    load_pops<TS, P, LD_NC, R>(f, dm, n, pv, fl, b, s, rec, rs);
+    load_pops<TS, P, LD, R>(f, dm, n, pv, fl, b, s, rec, rs);
     C u[3], inv_rho;
     mix_velocity<C, C2>(f, rho, F, s, inv_rho, u);
     collide<C, C2>(f, rho, inv_rho, u, F, s);

@@ -4,6 +4,8 @@
 
 #include <cstdlib>
 
+#include "lbm_persist.cuh"
+
 namespace lbm {
 
 static inline unsigned grid_for(long long n, int threads) { return (unsigned)((n + threads - 1) / threads); }
@@ -167,6 +169,34 @@ int Ops<TS>::pipe_blocks_per_sm()
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_pipe<TS, 0>, kChunk, 0);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_pipe<TS, 1>, kChunk, 0);
     return a < b ? a : b;
+}
+
+template <typename TS>
+cudaError_t Ops<TS>::persist(const BatchTable &t, const PersistArgs &pa, int grid, int block, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)block);
+    cfg.dynamicSmemBytes = slot_rec_bytes(1, block);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_persist<TS>, t, pa);
+}
+
+template <typename TS>
+int Ops<TS>::persist_grid(int block)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persist<TS>, block, slot_rec_bytes(1, block)) !=
+        cudaSuccess)
+        return 0;
+    return per * sms;
 }
 
 }  // namespace lbm

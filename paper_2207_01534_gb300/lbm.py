@@ -21,7 +21,7 @@ STATUS = {0: "LBM_OK", -1: "LBM_ERR_ARG", -2: "LBM_ERR_ALLOC", -3: "LBM_ERR_CUDA
           -5: "LBM_ERR_DRIFT", -6: "LBM_ERR_TIMEOUT", -7: "LBM_ERR_UNSUPPORTED"}
 BC = {"neem": 0, "zou_he": 1}
 STORAGE = {"fp32": 0, "fp64": 1, "fp16dev": 2, "bf16dev": 3}
-KERNEL = {"auto": 0, "split": 1, "fused": 2, "wave": 3, "push": 4, "brick": 5, "flow": 6}
+KERNEL = {"auto": 0, "split": 1, "fused": 2, "wave": 3, "push": 4, "brick": 5, "flow": 6, "persistent": 7}
 FIELDS = ("rho1", "rho2", "ux", "uy", "uz", "P")
 
 
@@ -390,6 +390,14 @@ class Batch:
 
     def set_stream(self, stream):
         self._c(self._lib.lbm_set_stream(self._h, ctypes.c_void_p(int(stream))))
+
+    def set_wait_limit(self, seconds: float):
+        """lbm_set_wait_limit: time limit of the persistent launch's grid barriers."""
+        self._c(self._lib.lbm_set_wait_limit(self._h, float(seconds)))
+
+    def inject_stall(self):
+        """lbm_inject_stall: one block of the next persistent launch never reaches its first barrier."""
+        self._c(self._lib.lbm_inject_stall(self._h))
 
     def autotune(self, cache_path=None) -> int:
         b = ctypes.c_int32(0)

@@ -100,6 +100,69 @@ def test_batch_samples_equal_their_solo_runs(lbm, storage):
         assert b[k].saturation() == solo.saturation()
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp16dev"])
+def test_persistent_batch_samples_equal_their_solo_runs(lbm, storage):
+    """One cooperative launch for many steps of the whole batch (grid barriers
+    between the passes): every sample bitwise its solo run, through a
+    parameter change of one sample between calls and launches that start on
+    either parity."""
+    cases = _cases()
+    b = lbm.Batch([dict(kw, storage=storage, kernel="persistent") for kw, _ in cases])
+    for smp, (_, rho) in zip(b.samples, cases):
+        smp.init_densities(*rho)
+    l0 = b.info()["launches"]
+    b.step(1)
+    b.step(37)
+    assert b.info()["launches"] - l0 == 2  # one launch per call of up to 256 steps
+    b[2].set_inlet(1.15)
+    b.step(9)
+    b.step(300)  # two launches
+    b.synchronize()
+    assert b.info()["step"] == 347
+    for k, (kw, rho) in enumerate(cases):
+        solo = _solo(lbm, kw, rho, 38, storage)
+        if k == 2:
+            solo.set_inlet(1.15)
+        solo.step(309)
+        a1, a2 = b[k].get_populations()
+        s1, s2 = solo.get_populations()
+        assert np.array_equal(a1, s1) and np.array_equal(a2, s2), "sample %d differs from its solo run" % k
+        assert b[k].saturation() == solo.saturation()
+
+
+def test_persistent_batch_barrier_timeout_is_reported(lbm):
+    """A block that never reaches its first grid barrier (lbm_inject_stall):
+    every wait gives up after the time limit, lbm_step reports
+    LBM_ERR_TIMEOUT, and after re-initialisation the batch steps as before."""
+    cases = _cases()[:2]
+    b = lbm.Batch([dict(kw, kernel="persistent") for kw, _ in cases])
+    for smp, (_, rho) in zip(b.samples, cases):
+        smp.init_densities(*rho)
+    b.step(4)
+    b.set_wait_limit(0.05)
+    b.inject_stall()
+    with pytest.raises(lbm.LbmError) as e:
+        b.step(3)
+        b.synchronize()
+    assert e.value.code == -6
+    for smp, (_, rho) in zip(b.samples, cases):
+        smp.init_densities(*rho)
+    b.step(20)
+    b.synchronize()
+    for k, (kw, rho) in enumerate(cases):
+        solo = _solo(lbm, kw, rho, 20, "fp32")
+        a1, a2 = b[k].get_populations()
+        s1, s2 = solo.get_populations()
+        assert np.array_equal(a1, s1) and np.array_equal(a2, s2)
+
+
+def test_persistent_launch_takes_batches_only(lbm):
+    kw, rho = _droplet()
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Lattice(**dict(kw, kernel="persistent"))
+    assert e.value.code == -7
+
+
 def test_batch_sample_matches_oracle(lbm):
     kw, rho = _open_slab(3)
     b = lbm.Batch([kw, _droplet()[0]])

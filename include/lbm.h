@@ -330,6 +330,14 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t *block_out
  * populations).  lbm_adjoint then computes the loss J of the final state and
  * runs the reverse pass: each segment of `every` steps is recomputed from its
  * checkpoint (keeping its every - 1 intermediate states), then reversed.
+ * With the split or wave schedule and reduce_every = 0, lbm_record also keeps the densities and
+ * virtual wall densities of every step (nsteps dense pairs over the voxels)
+ * when they take at most a quarter of the free device memory: its steps then
+ * run one launch sequence at a time (no graph), each writing its densities
+ * into its own slot, and the reverse pass recomputes only the collide-stream
+ * pass of each state (and the open-plane rule), not its density and wall
+ * passes.  The gradient is the same bit for bit; the environment variable
+ * LBM_RECORD_DENSITIES=0 turns the kept densities off.
  * Outputs: grad_xi (device pointer to nx*ny*nz floats, or NULL) receives
  * dloss * dJ/dxi on wall voxels and 0 elsewhere; *grad_rho_in1 (host, or
  * NULL) receives dloss * dJ/drho_in1 (0 without open planes); *loss (host, or

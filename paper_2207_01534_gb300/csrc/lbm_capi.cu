@@ -118,6 +118,12 @@ struct lbm_ctx {
         void *final_state = nullptr;
         std::vector<void *> seg;   // states inside one segment
         std::vector<void *> psis;  // densities (psi) of each state of a segment
+        // densities of every recorded step, written by the recording steps
+        // themselves when they fit (then the reverse pass recomputes only the
+        // collide-stream pass of each state, not its density and wall passes)
+        void *dens_all = nullptr;
+        size_t dens_all_bytes = 0;
+        bool dens_stored = false;
         void *lam[2] = {nullptr, nullptr}, *rb[2] = {nullptr, nullptr};
         void *abar = nullptr, *wbar = nullptr, *psi = nullptr;
         double *gxi = nullptr, *grin = nullptr;
@@ -1199,6 +1205,10 @@ void free_record(lbm_ctx *c)
             dfree(c, *q);
             *q = nullptr;
         }
+    if (r.dens_all) dfree(c, r.dens_all);
+    r.dens_all = nullptr;
+    r.dens_all_bytes = 0;
+    r.dens_stored = false;
     if (r.gxi) dfree(c, r.gxi);
     if (r.grin) dfree(c, r.grin);
     r.gxi = r.grin = nullptr;
@@ -2559,11 +2569,45 @@ lbm_status lbm_record(lbm_ctx *c, int64_t nsteps, int32_t every)
     r.step0 = c->step;
     r.n = nsteps;
     r.every = every;
+    // the densities of every step, if they take at most a quarter of the free
+    // device memory (LBM_RECORD_DENSITIES=0: never)
+    const size_t pb = (size_t)c->nv * (c->storage == LBM_STORE_FP64 ? 16 : 8);
+    const size_t dens_need = pb * (size_t)nsteps;
+    // (the split passes write them into c->s.psi; the other schedules keep
+    // their densities elsewhere, and a periodic check runs a density pass of
+    // the next state after its step, so those recompute them)
+    bool store = !(std::getenv("LBM_RECORD_DENSITIES") && std::atoi(std::getenv("LBM_RECORD_DENSITIES")) == 0) &&
+                 (c->kernel == LBM_KERNEL_SPLIT || c->kernel == LBM_KERNEL_WAVE) && c->p.reduce_every == 0;
+    if (store && r.dens_all_bytes < dens_need) {
+        if (r.dens_all) dfree(c, r.dens_all);
+        r.dens_all = nullptr;
+        r.dens_all_bytes = 0;
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess && dens_need <= fr / 4) r.dens_all = dalloc(c, dens_need);
+        if (r.dens_all) r.dens_all_bytes = dens_need;
+    }
+    store = store && r.dens_all && r.dens_all_bytes >= dens_need;
+    r.dens_stored = store;
     for (int64_t k = 0; k < nck; ++k) {
         snap_save(c, r.ckpt[(size_t)k]);
         const int64_t len = std::min<int64_t>(every, nsteps - k * every);
-        lbm_status st = lbm_step(c, len);
-        if (st != LBM_OK) return st;
+        if (store) {
+            // one step at a time, each writing its densities (and wall
+            // densities) into its own slot of dens_all
+            void *psi0 = c->s.psi;
+            for (int64_t q = 0; q < len; ++q) {
+                c->s.psi = (char *)r.dens_all + (size_t)(k * every + q) * pb;
+                lbm_status st = lbm_step(c, 1);
+                if (st != LBM_OK) {
+                    c->s.psi = psi0;
+                    return st;
+                }
+            }
+            c->s.psi = psi0;
+        } else {
+            lbm_status st = lbm_step(c, len);
+            if (st != LBM_OK) return st;
+        }
     }
     snap_save(c, r.final_state);
     r.step_end = c->step;
@@ -2588,7 +2632,7 @@ lbm_status lbm_adjoint(lbm_ctx *c, double dloss, float *grad_xi, double *grad_rh
         if (!q) return fail(c, LBM_ERR_ALLOC, "lbm_adjoint: segment states");
         r.seg.push_back(q);
     }
-    while ((int64_t)r.psis.size() < r.every) {
+    while (!r.dens_stored && (int64_t)r.psis.size() < r.every) {
         void *q = dalloc(c, (size_t)c->nv * (c->storage == LBM_STORE_FP64 ? 16 : 8));
         if (!q) return fail(c, LBM_ERR_ALLOC, "lbm_adjoint: segment densities");
         r.psis.push_back(q);
@@ -2649,24 +2693,42 @@ lbm_status lbm_adjoint(lbm_ctx *c, double dloss, float *grad_xi, double *grad_rh
         S[0] = r.ckpt[(size_t)k];
         for (int64_t q = 1; q < len; ++q) S[(size_t)q] = r.seg[(size_t)q - 1];
         S[(size_t)len] = k + 1 < nck ? r.ckpt[(size_t)k + 1] : r.final_state;
+        // densities of state q of the segment: recorded, or recomputed into psis[q]
+        const size_t pb = (size_t)c->nv * csz;
+        auto psi_of = [&](int64_t q) -> void * {
+            return r.dens_stored ? (void *)((char *)r.dens_all + (size_t)(t0 + q) * pb) : r.psis[(size_t)q];
+        };
         for (int64_t q = 0; q < len; ++q) {
             const int64_t step = r.step0 + t0 + q;
             const int par = (int)(step & 1);
-            const DevState s_q = snap_state(c, S[(size_t)q], r.psis[(size_t)q]);
-            const DevState s_n = snap_state(c, S[(size_t)q + 1], r.psis[(size_t)q]);
+            const DevState s_q = snap_state(c, S[(size_t)q], psi_of(q));
+            const DevState s_n = snap_state(c, S[(size_t)q + 1], psi_of(q));
             dispatch_adj(c, [&](auto tag) {
                 using TS = decltype(tag);
-                Ops<TS>::dens(s_q, par, step > 0, st, c->block);
-                Ops<TS>::wall(s_q, st, c->block);
-                if (q + 1 < len) Adj<TS>::fused_to(s_q, par, s_n.f, s_n.rest, st);
+                if (r.dens_stored) {
+                    // the checkpoint already holds its open-plane rule; a
+                    // recomputed state gets it here, as the density pass
+                    // would apply it
+                    if (q > 0 && step > 0) {
+                        Ops<TS>::plane(s_q, par, st);
+                        c->launches += s_q.open_z && s_q.nxy > 0 ? 1 : 0;
+                    }
+                } else {
+                    Ops<TS>::dens(s_q, par, step > 0, st, c->block);
+                    Ops<TS>::wall(s_q, st, c->block);
+                    c->launches += 2;
+                }
+                if (q + 1 < len) {
+                    Adj<TS>::fused_to(s_q, par, s_n.f, s_n.rest, st);
+                    c->launches += 1;
+                }
             });
-            c->launches += q + 1 < len ? 3 : 2;
         }
         // reverse the segment's steps
         for (int64_t q = len - 1; q >= 0; --q) {
             const int par = (int)((r.step0 + t0 + q) & 1);
-            const DevState s_t = snap_state(c, S[(size_t)q], r.psis[(size_t)q]);
-            const DevState s_n = snap_state(c, S[(size_t)q + 1], r.psis[(size_t)q]);
+            const DevState s_t = snap_state(c, S[(size_t)q], psi_of(q));
+            const DevState s_n = snap_state(c, S[(size_t)q + 1], psi_of(q));
             dispatch_adj(c, [&](auto tag) {
                 using TS = decltype(tag);
                 if (c->nz > 3) {

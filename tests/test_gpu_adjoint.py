@@ -92,6 +92,31 @@ def test_checkpoint_interval_does_not_change_the_gradient(lbm):
             assert J == ref[0] and grin == ref[2] and np.array_equal(gx, ref[1]), every
 
 
+@pytest.mark.parametrize("storage", ["fp32", "fp64"])
+def test_recorded_densities_give_the_recomputed_gradient(lbm, storage):
+    """The recording steps keep every step's densities when they fit, and the
+    reverse pass then recomputes only the collide-stream pass of each state;
+    with LBM_RECORD_DENSITIES=0 it recomputes the density and wall passes too.
+    Both give the same gradient, bit for bit, for full and ragged segments."""
+    import os
+
+    case = _case(nsteps=23)
+    out = []
+    for flag in (None, "0"):
+        old = os.environ.pop("LBM_RECORD_DENSITIES", None)
+        if flag is not None:
+            os.environ["LBM_RECORD_DENSITIES"] = flag
+        try:
+            _, J, gx, grin = _gpu_grad(lbm, storage, case, 5)
+        finally:
+            os.environ.pop("LBM_RECORD_DENSITIES", None)
+            if old is not None:
+                os.environ["LBM_RECORD_DENSITIES"] = old
+        out.append((J, gx, grin))
+    assert out[0][0] == out[1][0] and out[0][2] == out[1][2] and np.array_equal(out[0][1], out[1][1])
+    assert np.abs(out[0][1]).max() > 0
+
+
 def test_adjoint_against_finite_differences(lbm):
     """Central differences (eps = 1e-3) of the CUDA forward in FP64 storage
     against the FP32 reverse pass: relative error <= 1e-2."""

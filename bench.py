@@ -619,9 +619,10 @@ def adjoint_line(args, world, dist, local):
     with torch.cuda.stream(stream):
         lat = lbm.Lattice(solid, storage="fp32", kernel="split", stream=stream.cuda_stream, **kw)
         gx = torch.zeros(solid.shape, dtype=torch.float32, device="cuda")
-        # warm-up: one short record + reverse pass
+        # warm-up: one record + reverse pass of the timed length, so the
+        # checkpoint, segment and density buffers are allocated before timing
         lat.init_densities(r1, r2)
-        lat.record(2 * every, every)
+        lat.record(nsteps, every)
         lat.adjoint(1.0, gx)
         barrier(dist)
         torch.cuda.synchronize()

@@ -337,7 +337,10 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t *block_out
  * into its own slot, and the reverse pass recomputes only the collide-stream
  * pass of each state (and the open-plane rule), not its density and wall
  * passes.  The gradient is the same bit for bit; the environment variable
- * LBM_RECORD_DENSITIES=0 turns the kept densities off.
+ * LBM_RECORD_DENSITIES=0 turns the kept densities off.  With kept densities,
+ * lbm_adjoint recomputes segment k - 1 on a private stream, into a second set
+ * of segment buffers, while it reverses segment k (LBM_ADJ_OVERLAP=0: one
+ * segment after the other); the gradient is again the same bit for bit.
  * Outputs: grad_xi (device pointer to nx*ny*nz floats, or NULL) receives
  * dloss * dJ/dxi on wall voxels and 0 elsewhere; *grad_rho_in1 (host, or
  * NULL) receives dloss * dJ/drho_in1 (0 without open planes); *loss (host, or

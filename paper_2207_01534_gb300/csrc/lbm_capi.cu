@@ -124,6 +124,11 @@ struct lbm_ctx {
         void *dens_all = nullptr;
         size_t dens_all_bytes = 0;
         bool dens_stored = false;
+        // a second set of segment states, a side stream and its events: the
+        // recompute of one segment overlaps the reverse of the next
+        std::vector<void *> seg2;
+        cudaStream_t side = nullptr;
+        cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
         void *lam[2] = {nullptr, nullptr}, *rb[2] = {nullptr, nullptr};
         void *abar = nullptr, *wbar = nullptr, *psi = nullptr;
         double *gxi = nullptr, *grin = nullptr;
@@ -991,6 +996,9 @@ void destroy_ctx(lbm_ctx *c)
     for (cudaStream_t st : c->wave_streams) cudaStreamDestroy(st);
     for (cudaEvent_t ev : c->wave_events) cudaEventDestroy(ev);
     free_record(c);
+    if (c->rec.side) cudaStreamDestroy(c->rec.side);
+    for (cudaEvent_t ev : c->rec.ev)
+        if (ev) cudaEventDestroy(ev);
     std::vector<std::pair<void *, size_t>> a = c->allocs;
     for (auto &q : a) dfree(c, q.first);
     if (c->h_flag) cudaFreeHost(c->h_flag);
@@ -1205,6 +1213,8 @@ void free_record(lbm_ctx *c)
             dfree(c, *q);
             *q = nullptr;
         }
+    for (void *q : r.seg2) dfree(c, q);
+    r.seg2.clear();
     if (r.dens_all) dfree(c, r.dens_all);
     r.dens_all = nullptr;
     r.dens_all_bytes = 0;
@@ -2681,28 +2691,35 @@ lbm_status lbm_adjoint(lbm_ctx *c, double dloss, float *grad_xi, double *grad_rh
     c->launches += 1;
 
     const int64_t nck = (int64_t)r.ckpt.size();
-    for (int64_t k = nck - 1; k >= 0; --k) {
-        const int64_t t0 = k * r.every;
-        const int64_t len = std::min<int64_t>(r.every, r.n - t0);
-        // Recompute the segment from its checkpoint, out of place: the
-        // density pass of state q (in its own buffer) applies the pending
-        // open-plane extrapolation and writes the densities of state q into
-        // psis[q]; the collide-stream pass reads state q and writes state q + 1
-        // into the next buffer.  The live state is not touched.
+    const size_t pb = (size_t)c->nv * csz;
+    // The states of segment k: its checkpoint, the every - 1 recomputed states
+    // in buffer set `set`, and the next checkpoint (or the final state).
+    auto states = [&](int64_t k, int set) {
+        const int64_t len = std::min<int64_t>(r.every, r.n - k * r.every);
         std::vector<void *> S((size_t)len + 1);
         S[0] = r.ckpt[(size_t)k];
-        for (int64_t q = 1; q < len; ++q) S[(size_t)q] = r.seg[(size_t)q - 1];
+        for (int64_t q = 1; q < len; ++q) S[(size_t)q] = (set ? r.seg2 : r.seg)[(size_t)q - 1];
         S[(size_t)len] = k + 1 < nck ? r.ckpt[(size_t)k + 1] : r.final_state;
-        // densities of state q of the segment: recorded, or recomputed into psis[q]
-        const size_t pb = (size_t)c->nv * csz;
-        auto psi_of = [&](int64_t q) -> void * {
-            return r.dens_stored ? (void *)((char *)r.dens_all + (size_t)(t0 + q) * pb) : r.psis[(size_t)q];
-        };
+        return S;
+    };
+    // densities of state q of segment k: recorded, or recomputed into psis[q]
+    auto psi_of = [&](int64_t k, int64_t q) -> void * {
+        return r.dens_stored ? (void *)((char *)r.dens_all + (size_t)(k * r.every + q) * pb) : r.psis[(size_t)q];
+    };
+    // Recompute segment k from its checkpoint, out of place, on stream s: with
+    // recorded densities, the open-plane rule on each recomputed state and the
+    // collide-stream pass; otherwise the density pass of state q (in its own
+    // buffer), which applies the pending open-plane rule and writes the
+    // densities of state q into psis[q], then the wall and collide-stream
+    // passes.  The live state is not touched.
+    auto recompute = [&](int64_t k, int set, cudaStream_t s) {
+        const std::vector<void *> S = states(k, set);
+        const int64_t len = (int64_t)S.size() - 1;
         for (int64_t q = 0; q < len; ++q) {
-            const int64_t step = r.step0 + t0 + q;
+            const int64_t step = r.step0 + k * r.every + q;
             const int par = (int)(step & 1);
-            const DevState s_q = snap_state(c, S[(size_t)q], psi_of(q));
-            const DevState s_n = snap_state(c, S[(size_t)q + 1], psi_of(q));
+            const DevState s_q = snap_state(c, S[(size_t)q], psi_of(k, q));
+            const DevState s_n = snap_state(c, S[(size_t)q + 1], psi_of(k, q));
             dispatch_adj(c, [&](auto tag) {
                 using TS = decltype(tag);
                 if (r.dens_stored) {
@@ -2710,25 +2727,29 @@ lbm_status lbm_adjoint(lbm_ctx *c, double dloss, float *grad_xi, double *grad_rh
                     // recomputed state gets it here, as the density pass
                     // would apply it
                     if (q > 0 && step > 0) {
-                        Ops<TS>::plane(s_q, par, st);
+                        Ops<TS>::plane(s_q, par, s);
                         c->launches += s_q.open_z && s_q.nxy > 0 ? 1 : 0;
                     }
                 } else {
-                    Ops<TS>::dens(s_q, par, step > 0, st, c->block);
-                    Ops<TS>::wall(s_q, st, c->block);
+                    Ops<TS>::dens(s_q, par, step > 0, s, c->block);
+                    Ops<TS>::wall(s_q, s, c->block);
                     c->launches += 2;
                 }
                 if (q + 1 < len) {
-                    Adj<TS>::fused_to(s_q, par, s_n.f, s_n.rest, st);
+                    Adj<TS>::fused_to(s_q, par, s_n.f, s_n.rest, s);
                     c->launches += 1;
                 }
             });
         }
-        // reverse the segment's steps
+    };
+    // Reverse the steps of segment k on the context's stream.
+    auto reverse = [&](int64_t k, int set) {
+        const std::vector<void *> S = states(k, set);
+        const int64_t len = (int64_t)S.size() - 1;
         for (int64_t q = len - 1; q >= 0; --q) {
-            const int par = (int)((r.step0 + t0 + q) & 1);
-            const DevState s_t = snap_state(c, S[(size_t)q], psi_of(q));
-            const DevState s_n = snap_state(c, S[(size_t)q + 1], psi_of(q));
+            const int par = (int)((r.step0 + k * r.every + q) & 1);
+            const DevState s_t = snap_state(c, S[(size_t)q], psi_of(k, q));
+            const DevState s_n = snap_state(c, S[(size_t)q + 1], psi_of(k, q));
             dispatch_adj(c, [&](auto tag) {
                 using TS = decltype(tag);
                 if (c->nz > 3) {
@@ -2744,6 +2765,52 @@ lbm_status lbm_adjoint(lbm_ctx *c, double dloss, float *grad_xi, double *grad_rh
             c->launches += 5;
             std::swap(a.lam_in, a.lam_out);
             std::swap(a.rb_in, a.rb_out);
+        }
+    };
+    // With recorded densities and a second set of segment buffers, segment
+    // k - 1 is recomputed on a side stream while segment k is reversed: the
+    // two touch disjoint buffers (the recompute writes only its own set and
+    // reads checkpoints and densities), and the reverse kernels leave most of
+    // the memory bandwidth free.  Otherwise segment by segment on one stream.
+    bool overlap = r.dens_stored && nck > 1 && r.every > 1 &&
+                   !(std::getenv("LBM_ADJ_OVERLAP") && std::atoi(std::getenv("LBM_ADJ_OVERLAP")) == 0);
+    if (overlap) {
+        while ((int64_t)r.seg2.size() < r.every - 1) {
+            void *q = dalloc(c, sb);
+            if (!q) break;
+            r.seg2.push_back(q);
+        }
+        overlap = (int64_t)r.seg2.size() >= r.every - 1;
+        if (overlap && !r.side) {
+            overlap = cudaStreamCreateWithFlags(&r.side, cudaStreamNonBlocking) == cudaSuccess;
+            for (int q = 0; overlap && q < 5; ++q)
+                overlap = cudaEventCreateWithFlags(&r.ev[q], cudaEventDisableTiming) == cudaSuccess;
+            if (!overlap) cudaGetLastError();
+        }
+    }
+    if (overlap) {
+        cudaStream_t side = r.side;
+        cudaEvent_t *rec_done = &r.ev[0], *rev_done = &r.ev[2];
+        cudaEventRecord(r.ev[4], st);  // everything enqueued so far (the seed) before the side stream starts
+        cudaStreamWaitEvent(side, r.ev[4], 0);
+        recompute(nck - 1, (int)((nck - 1) & 1), side);
+        cudaEventRecord(rec_done[(nck - 1) & 1], side);
+        for (int64_t k = nck - 1; k >= 0; --k) {
+            const int set = (int)(k & 1);
+            if (k >= 1) {
+                const int oset = (int)((k - 1) & 1);
+                if (k + 1 < nck) cudaStreamWaitEvent(side, rev_done[oset], 0);  // segment k + 1 used that set
+                recompute(k - 1, oset, side);
+                cudaEventRecord(rec_done[oset], side);
+            }
+            cudaStreamWaitEvent(st, rec_done[set], 0);
+            reverse(k, set);
+            cudaEventRecord(rev_done[set], st);
+        }
+    } else {
+        for (int64_t k = nck - 1; k >= 0; --k) {
+            recompute(k, 0, st);
+            reverse(k, 0);
         }
     }
     // the recompute never touched the live state: it is still the final one

@@ -333,8 +333,10 @@ lbm_status lbm_autotune(lbm_ctx *ctx, const char *cache_path, int32_t *block_out
  * With the split or wave schedule and reduce_every = 0, lbm_record also keeps the densities and
  * virtual wall densities of every step (nsteps dense pairs over the voxels)
  * when they take at most a quarter of the free device memory: its steps then
- * run one launch sequence at a time (no graph), each writing its densities
- * into its own slot, and the reverse pass recomputes only the collide-stream
+ * each write their densities into their own slot (the whole recording is
+ * captured as one CUDA graph the first time and replayed while its length,
+ * buffers, starting parity and parameters stay the same; LBM_NO_GRAPH turns
+ * that off), and the reverse pass recomputes only the collide-stream
  * pass of each state (and the open-plane rule), not its density and wall
  * passes.  The gradient is the same bit for bit; the environment variable
  * LBM_RECORD_DENSITIES=0 turns the kept densities off.  With kept densities,

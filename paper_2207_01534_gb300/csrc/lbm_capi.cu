@@ -129,6 +129,13 @@ struct lbm_ctx {
         std::vector<void *> seg2;
         cudaStream_t side = nullptr;
         cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+        // the recording steps with kept densities as one CUDA graph, replayed
+        // while the recording's shape, buffers, parity and parameters stay
+        cudaGraphExec_t graph = nullptr;
+        std::vector<void *> graph_key;  // buffers it writes
+        int64_t graph_n = 0, graph_every = 0, graph_launches = 0;
+        int graph_par = -1, graph_block = 0;
+        DevState graph_state{};  // the kernel arguments it holds (every parameter and pointer)
         void *lam[2] = {nullptr, nullptr}, *rb[2] = {nullptr, nullptr};
         void *abar = nullptr, *wbar = nullptr, *psi = nullptr;
         double *gxi = nullptr, *grin = nullptr;
@@ -997,6 +1004,7 @@ void destroy_ctx(lbm_ctx *c)
     for (cudaEvent_t ev : c->wave_events) cudaEventDestroy(ev);
     free_record(c);
     if (c->rec.side) cudaStreamDestroy(c->rec.side);
+    if (c->rec.graph) cudaGraphExecDestroy(c->rec.graph);
     for (cudaEvent_t ev : c->rec.ev)
         if (ev) cudaEventDestroy(ev);
     std::vector<std::pair<void *, size_t>> a = c->allocs;
@@ -2598,7 +2606,74 @@ lbm_status lbm_record(lbm_ctx *c, int64_t nsteps, int32_t every)
     }
     store = store && r.dens_all && r.dens_all_bytes >= dens_need;
     r.dens_stored = store;
-    for (int64_t k = 0; k < nck; ++k) {
+    // with kept densities, the whole recording as one graph: captured the
+    // first time, replayed while nothing it holds has changed
+    const bool use_graph = store && std::getenv("LBM_NO_GRAPH") == nullptr;
+    if (use_graph) {
+        std::vector<void *> key = r.ckpt;
+        key.push_back(r.final_state);
+        key.push_back(r.dens_all);
+        key.push_back(c->s.psi);
+        key.push_back(c->s.f);
+        const int par0 = (int)(c->step & 1) + (c->step > 0 ? 2 : 0);
+        if (r.graph && (r.graph_key != key || r.graph_n != nsteps || r.graph_every != every ||
+                        r.graph_par != par0 || r.graph_block != c->block ||
+                        std::memcmp(&r.graph_state, &c->s, sizeof(DevState)) != 0)) {
+            cudaGraphExecDestroy(r.graph);
+            r.graph = nullptr;
+        }
+        if (r.graph) {
+            cudaError_t e = cudaGraphLaunch(r.graph, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "lbm_record: graph");
+            c->step += nsteps;
+            c->launches += r.graph_launches;
+        } else {
+            if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+                return cuda_fail(c, cudaGetLastError(), "lbm_record: capture stream");
+            // the capture stream starts after the work already on the context's stream
+            cudaEvent_t ev0 = nullptr;
+            cudaEventCreateWithFlags(&ev0, cudaEventDisableTiming);
+            cudaEventRecord(ev0, c->stream);
+            cudaStreamWaitEvent(c->cap_stream, ev0, 0);
+            const cudaStream_t user = c->stream;
+            const int64_t step0 = c->step, l0 = c->launches;
+            void *psi0 = c->s.psi;
+            c->stream = c->cap_stream;
+            cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+            lbm_status sst = LBM_OK;
+            for (int64_t k = 0; e == cudaSuccess && sst == LBM_OK && k < nck; ++k) {
+                snap_save(c, r.ckpt[(size_t)k]);
+                const int64_t len = std::min<int64_t>(every, nsteps - k * every);
+                for (int64_t q = 0; q < len && sst == LBM_OK; ++q) {
+                    c->s.psi = (char *)r.dens_all + (size_t)(k * every + q) * pb;
+                    step_once(c);
+                }
+            }
+            c->s.psi = psi0;
+            cudaGraph_t g = nullptr;
+            cudaError_t e2 = e == cudaSuccess ? cudaStreamEndCapture(c->cap_stream, &g) : e;
+            c->stream = user;
+            if (e2 == cudaSuccess) e2 = cudaGraphInstantiate(&r.graph, g, 0);
+            if (g) cudaGraphDestroy(g);
+            cudaEventDestroy(ev0);
+            if (e2 != cudaSuccess) {
+                r.graph = nullptr;
+                cudaGetLastError();
+                return cuda_fail(c, e2, "lbm_record: graph capture");
+            }
+            r.graph_key = key;
+            r.graph_n = nsteps;
+            r.graph_every = every;
+            r.graph_par = par0;
+            r.graph_block = c->block;
+            std::memcpy(&r.graph_state, &c->s, sizeof(DevState));
+            r.graph_launches = c->launches - l0;
+            (void)step0;
+            e = cudaGraphLaunch(r.graph, c->stream);
+            if (e != cudaSuccess) return cuda_fail(c, e, "lbm_record: graph");
+        }
+    }
+    for (int64_t k = 0; !use_graph && k < nck; ++k) {
         snap_save(c, r.ckpt[(size_t)k]);
         const int64_t len = std::min<int64_t>(every, nsteps - k * every);
         if (store) {

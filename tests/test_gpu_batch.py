@@ -161,6 +161,17 @@ def test_persistent_launch_takes_batches_only(lbm):
     with pytest.raises(lbm.LbmError) as e:
         lbm.Lattice(**dict(kw, kernel="persistent"))
     assert e.value.code == -7
+    # the batch table of one launch holds at most 96 samples
+    tiny = dict(solid=np.zeros((4, 4, 4), np.uint8), tau=(1.0, 1.0), G=3.5, kernel="persistent")
+    with pytest.raises(lbm.LbmError) as e:
+        lbm.Batch([tiny] * 97)
+    assert e.value.code == -7
+    b = lbm.Batch([tiny] * 96)
+    for smp in b.samples:
+        smp.init_densities(np.full((4, 4, 4), 0.5), np.full((4, 4, 4), 0.5))
+    b.step(3)
+    b.synchronize()
+    assert b.info()["step"] == 3
 
 
 def test_batch_sample_matches_oracle(lbm):

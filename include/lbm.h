@@ -375,6 +375,20 @@ lbm_status lbm_adjoint(lbm_ctx *ctx, double dloss, float *grad_xi, double *grad_
 lbm_status lbm_set_wait_limit(lbm_ctx *ctx, double seconds);
 lbm_status lbm_inject_stall(lbm_ctx *ctx);
 
+/* ---- Checkpoint / resume (the paper has none) ----------------------------
+ * lbm_save writes the lattice's state to a file: every population cell (in
+ * the storage type, as stored), the open-plane boundary cells, the frozen
+ * missing populations of the open planes, the step count, the deviation
+ * reference densities of 16-bit storage and the initial masses of the drift
+ * check, behind a header that names the storage type, the grid and a hash of
+ * the solid mask.  lbm_load reads such a file into a lattice created with
+ * the same geometry and storage type (LBM_ERR_ARG for any other file, or one
+ * that is truncated) and sets its step count; stepping on from there gives
+ * bitwise the results of the uninterrupted run.  Both synchronise; a sample
+ * of a batch can be saved and loaded, a batch itself cannot (LBM_ERR_ARG). */
+lbm_status lbm_save(lbm_ctx *ctx, const char *path);
+lbm_status lbm_load(lbm_ctx *ctx, const char *path);
+
 /* Largest n accepted by lbm_saturation_static. */
 #define LBM_SATURATION_STATIC_MAX_N 16777216
 

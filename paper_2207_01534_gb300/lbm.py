@@ -91,6 +91,8 @@ def load(build_if_missing: bool = True):
     lib.lbm_batch_size.argtypes = [P]
     lib.lbm_batch_size.restype = ctypes.c_int32
     lib.lbm_batch_get.argtypes = [P, ctypes.c_int32, ctypes.POINTER(P)]
+    lib.lbm_save.argtypes = [P, ctypes.c_char_p]
+    lib.lbm_load.argtypes = [P, ctypes.c_char_p]
     lib.lbm_autotune.argtypes = [P, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]
     lib.lbm_set_xi_field.argtypes = [P, P, ctypes.c_int32]
     lib.lbm_record.argtypes = [P, ctypes.c_int64, ctypes.c_int32]
@@ -102,7 +104,7 @@ def load(build_if_missing: bool = True):
                  "lbm_set_populations", "lbm_get_populations", "lbm_step", "lbm_step_timed", "lbm_read_fields",
                  "lbm_saturation", "lbm_saturation_static", "lbm_set_inlet", "lbm_set_stream", "lbm_synchronize",
                  "lbm_get_info", "lbm_create_batch", "lbm_batch_get", "lbm_autotune", "lbm_set_xi_field",
-                 "lbm_record", "lbm_adjoint", "lbm_set_wait_limit", "lbm_inject_stall"):
+                 "lbm_record", "lbm_adjoint", "lbm_set_wait_limit", "lbm_inject_stall", "lbm_save", "lbm_load"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -241,6 +243,14 @@ class Lattice:
         else:
             a = np.ascontiguousarray(np.broadcast_to(xi, self.shape), dtype=np.float32)
             self._c(self._lib.lbm_set_xi_field(self._h, a.ctypes.data, 0))
+
+    def save(self, path: str):
+        """lbm_save: the lattice's state (populations, boundary cells, step count) to a file."""
+        self._c(self._lib.lbm_save(self._h, str(path).encode()))
+
+    def load(self, path: str):
+        """lbm_load: the state saved by ``save`` into a lattice of the same geometry and storage."""
+        self._c(self._lib.lbm_load(self._h, str(path).encode()))
 
     def set_wait_limit(self, seconds: float):
         """lbm_set_wait_limit: time limit of the single-pass schedule's device waits."""

@@ -363,6 +363,12 @@ def other_forms(args, lbm, solid, r1, r2, kw, nf, value, dist, local):
                       "batch_over_solo": b["config"]["batch_over_solo"],
                       "solo_sequential_mlups": b["config"]["solo_sequential_mlups"],
                       "step_frac": b["roofline"]["frac"]}
+    # the same batch stepped by one persistent cooperative launch per 256 steps
+    sub.kernel = "persistent"
+    bp = batch_line(sub, 1, dist, local, solo=False)
+    forms["batch_persistent"] = {"workload": BATCH_WORKLOAD, "value": bp["value"], "unit": UNIT, "steps": sub.steps,
+                                 "gpu_launches": bp["gpu_launches"], "over_batch": bp["value"] / b["value"],
+                                 "over_solo": bp["value"] / b["config"]["solo_sequential_mlups"]}
     a = adjoint_line(args, 1, dist, local)
     forms["adjoint"] = {"workload": ADJOINT_WORKLOAD, "value": a["value"], "unit": UNIT, "steps": a["steps"],
                         "adjoint_over_forward_time": a["config"]["adjoint_over_forward_time"],
@@ -495,7 +501,7 @@ def run_batch(args, rank, world):
     dist_finish(dist)
 
 
-def batch_line(args, world, dist, local):
+def batch_line(args, world, dist, local, solo=True):
     import tempfile
 
     samples, states, cfg = batch_setup(args.batch_count, tuple(args.batch_edges))
@@ -538,22 +544,126 @@ def batch_line(args, world, dist, local):
         torch.cuda.synchronize()
 
         # the same samples as solo lattices stepped one after another
-        solo = []
-        for kw, (r1, r2) in zip(samples, states):
+    # end to end through the public API with host buffers: create (geometry
+    # upload), initial densities upload, K steps, fields and saturation read
+    # back.  The inputs sit in pinned host memory (the binding passes
+    # contiguous arrays through, so the library copies from these buffers).
+    solid_h = torch.from_numpy(np.ascontiguousarray(solid, dtype=np.uint8)).pin_memory().numpy()
+    r1_h = torch.from_numpy(np.ascontiguousarray(r1, dtype=np.float64)).pin_memory().numpy()
+    r2_h = torch.from_numpy(np.ascontiguousarray(r2, dtype=np.float64)).pin_memory().numpy()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lat2 = lbm.Lattice(solid_h, kernel=args.kernel, storage=args.storage, **kw)
+    lat2.init_densities(r1_h, r2_h)
+    lat2.step(args.steps)
+    fields = lat2.fields(("rho1", "rho2"))
+    s2 = lat2.saturation()
+    dt = time.perf_counter() - t0
+    del lat2, fields
+    h2d = solid.nbytes + r1.nbytes + r2.nbytes
+    d2h = 2 * nvox * 8 + 4 * 8
+    e2e = {"value": nf * args.steps / dt / 1e6, "unit": UNIT, "h2d_bytes_per_step": h2d / args.steps,
+           "d2h_bytes_per_step": d2h / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+
+        v, done, cdt = oracle_rate(solid, r1, r2, kw, steps=args.cpu_steps)
+        oracle.set_threads(1)
+        v1, done1, cdt1 = oracle_rate(solid, r1, r2, kw, steps=3, budget_s=15.0)
+        oracle.set_threads(os.cpu_count() or 1)
+        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d full steps of the %s workload (%.1f s); one core: %d steps (%.1f s)" % (
+                   done, WORKLOAD, cdt, done1, cdt1),
+               "value_one_core": v1}
+    cfg = dict(cfg)
+    cfg.update({"parallelism": "replicas" if world > 1 else "single", "kernel_schedule": args.kernel,
+                "storage": args.storage,
+                "voxel_mlups": nvox * args.steps * world / (ms / 1e3) / 1e6})
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE[args.storage], "data": "synthetic", "config": cfg, "roofline": roof,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+            "saturation": {"S_w": sat[0], "S_nw_smooth": sat[1]}}
+    if world == 1 and not args.no_forms and args.kernel == "auto" and args.storage == "fp32":
+        line["forms"] = other_forms(args, lbm, solid, r1, r2, kw, nf, value, dist, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist_finish(dist)
+
+
+def run_batch(args, rank, world):
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = dist_init(world)
+    line = batch_line(args, world, dist, local)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist_finish(dist)
+
+
+def batch_line(args, world, dist, local, solo=True):
+    import tempfile
+
+    samples, states, cfg = batch_setup(args.batch_count, tuple(args.batch_edges))
+    import torch
+
+    from paper_2207_01534_gb300 import lbm
+
+    lbm.load()
+    nf = cfg["n_fluid_total"]
+    stream = torch.cuda.Stream()
+    cache = args.tune_cache or os.path.join(tempfile.gettempdir(), "lbm_autotune.json")
+    with torch.cuda.stream(stream):
+        bkern = "persistent" if args.kernel == "persistent" else "split"
+        b = lbm.Batch([dict(kw, storage=args.storage, kernel=bkern) for kw in samples], stream=stream.cuda_stream)
+        for smp, (r1, r2) in zip(b.samples, states):
+            smp.init_densities(r1, r2)
+        b.step(args.warmup)
+        block = b.autotune(cache)
+        b.step(2)
+        b.synchronize()
+        clocks = ClockSampler(local)
+        l0 = b.info()["launches"]
+        barrier(dist)
+        torch.cuda.synchronize()
+        clocks.start()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        b.step(args.steps)
+        ev1.record(stream)
+        clocks.snapshot()
+        torch.cuda.synchronize()
+        clocks.snapshot()
+        clk = clocks.stop()
+        launches = b.info()["launches"] - l0
+        ms = max_over_ranks(dist, ev0.elapsed_time(ev1), "cuda")
+        sats = [smp.saturation() for smp in b.samples]
+        assert np.isfinite(np.array(sats)).all()
+        b.close()
+        del b
+        torch.cuda.synchronize()
+
+        # the same samples as solo lattices stepped one after another
+        solo_runs = []
+        for kw, (r1, r2) in zip(samples, states) if solo else []:
             g = lbm.Lattice(kernel="split", storage=args.storage, stream=stream.cuda_stream, **kw)
             g.init_densities(r1, r2)
             g.step(args.warmup + 2)
-            solo.append(g)
+            solo_runs.append(g)
         torch.cuda.synchronize()
         ev0.record(stream)
-        for g in solo:
+        for g in solo_runs:
             g.step(args.steps)
         ev1.record(stream)
         torch.cuda.synchronize()
-        ms_solo = ev0.elapsed_time(ev1)
-        for g in solo:
+        ms_solo = ev0.elapsed_time(ev1) if solo else float("nan")
+        for g in solo_runs:
             g.close()
-        del solo
+        del solo_runs
         torch.cuda.synchronize()
 
     # end to end through the public API with host buffers

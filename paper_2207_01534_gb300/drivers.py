@@ -16,13 +16,38 @@ time step runs in liblbm's CUDA kernels).
 """
 from __future__ import annotations
 
+import json
 import math
+import time
 
 import numpy as np
 
 from . import inputs
 
 CS2 = 1.0 / 3.0
+
+
+class JsonLines:
+    """Append one JSON object per line to ``path`` (a run's time series: one
+    record per stage or checkpoint, each stamped with the wall-clock time and
+    the lattice's step count and launch count).  ``None`` writes nothing."""
+
+    def __init__(self, path, lattice=None, **run):
+        self.path, self.lattice = path, lattice
+        if path is not None and run:
+            self.write({"run": run})
+
+    def write(self, rec):
+        if self.path is None:
+            return
+        rec = dict(rec)
+        rec["time"] = time.time()
+        if self.lattice is not None and hasattr(self.lattice, "info"):
+            info = self.lattice.info()
+            rec.setdefault("lattice_step", int(info["step"]))
+            rec.setdefault("launches", int(info["launches"]))
+        with open(self.path, "a") as fh:
+            fh.write(json.dumps(rec) + "\n")
 
 
 def pressure(rho1, rho2, G):
@@ -37,12 +62,15 @@ def inlet_density(pc, G=3.5, minor=0.03, rho_out2=1.0):
     return (p_out + pc - CS2 * minor) / (CS2 * (1.0 + G * minor))
 
 
-def pc_sw_curve(lattice, pcs, G=3.5, minor=0.03, rho_out2=1.0, max_steps=20000, check_every=500, tol=1e-3):
+def pc_sw_curve(lattice, pcs, G=3.5, minor=0.03, rho_out2=1.0, max_steps=20000, check_every=500, tol=1e-3,
+                log=None):
     """Raise the inlet density through the capillary pressures ``pcs`` (in
     order).  At each stage the lattice steps in chunks of ``check_every`` until
     the water saturation changes by less than ``tol`` over a chunk, or
     ``max_steps`` have run.  Returns one dict per stage: pc, rho_in1, S_w,
-    smooth S_nw, steps, settled."""
+    smooth S_nw, steps, settled; with ``log`` (a path) each stage is also
+    appended to that file as a JSON line."""
+    jl = JsonLines(log, lattice, driver="pc_sw_curve", pcs=[float(p) for p in pcs], G=G, tol=tol)
     out = []
     for pc in pcs:
         rin = inlet_density(pc, G, minor, rho_out2)
@@ -60,6 +88,7 @@ def pc_sw_curve(lattice, pcs, G=3.5, minor=0.03, rho_out2=1.0, max_steps=20000, 
         sw, snw = lattice.saturation()[:2]
         out.append({"pc": float(pc), "rho_in1": float(rin), "S_w": float(sw), "S_nw_smooth": float(snw),
                     "steps": int(steps), "settled": settled})
+        jl.write(out[-1])
     return out
 
 
@@ -111,20 +140,25 @@ def trapped_volume(rho1, rho2, solid, outlet_slices, periodic_xy=(True, True)):
     return int(((lab > 0) & ~np.isin(root[lab], connected)).sum())
 
 
-def drainage_history(lattice, solid, nsteps, every=500, outlet_slices=8, periodic_xy=(True, True)):
+def drainage_history(lattice, solid, nsteps, every=500, outlet_slices=8, periodic_xy=(True, True), log=None):
     """Step a drainage ``nsteps`` steps, recording every ``every`` steps the
-    water saturation S_w, the smooth non-wetting saturation and the trapped
-    wetting volume (Section 4.1 outputs).  Returns a list of dicts."""
+    water saturation S_w, the smooth non-wetting saturation, the component
+    masses and the trapped wetting volume (Section 4.1 outputs).  Returns a
+    list of dicts; with ``log`` (a path) each record is also appended to that
+    file as a JSON line."""
+    jl = JsonLines(log, lattice, driver="drainage_history", nsteps=int(nsteps), every=int(every))
     out = []
     done = 0
     while done < nsteps:
         k = min(every, nsteps - done)
         lattice.step(k)
         done += k
-        sw, snw = lattice.saturation()[:2]
+        sw, snw, m1, m2 = (list(lattice.saturation()) + [float("nan")] * 4)[:4]
         f = lattice.fields(("rho1", "rho2"))
-        out.append({"step": done, "S_w": float(sw), "S_nw_smooth": float(snw),
+        out.append({"step": done, "S_w": float(sw), "S_nw_smooth": float(snw), "mass1": float(m1),
+                    "mass2": float(m2),
                     "trapped": trapped_volume(f["rho1"], f["rho2"], solid, outlet_slices, periodic_xy)})
+        jl.write(out[-1])
     return out
 
 

@@ -61,3 +61,52 @@ def test_trapped_volume_counts_only_cut_off_water():
     # solid voxels never count
     solid[2:4, 1:3, 1:3] = 1
     assert drivers.trapped_volume(rho1, rho2, solid, 3) == 1
+
+
+class _StandInLattice:
+    """A stand-in with the Lattice calls the drivers use: S_w falls by a fixed
+    amount per step until it reaches a floor; the fields are uniform."""
+
+    def __init__(self, solid):
+        self.solid = solid
+        self.steps = 0
+        self.rin = None
+
+    def step(self, n):
+        self.steps += n
+
+    def set_inlet(self, rin):
+        self.rin = rin
+
+    def saturation(self):
+        sw = max(0.3, 1.0 - 1e-4 * self.steps)
+        return (sw, 1.0 - sw, 100.0, 200.0)
+
+    def fields(self, names):
+        shape = self.solid.shape
+        return {"rho1": np.full(shape, 0.03), "rho2": np.full(shape, 1.0)}
+
+    def info(self):
+        return {"step": self.steps, "launches": 3 * self.steps}
+
+
+def test_drivers_write_json_lines(tmp_path):
+    import json
+
+    solid = np.zeros((10, 4, 4), np.uint8)
+    lat = _StandInLattice(solid)
+    log = tmp_path / "hist.jsonl"
+    hist = drivers.drainage_history(lat, solid, 1200, every=500, outlet_slices=2, log=log)
+    assert [h["step"] for h in hist] == [500, 1000, 1200]
+    recs = [json.loads(line) for line in log.read_text().splitlines()]
+    assert recs[0]["run"]["driver"] == "drainage_history"
+    assert [r["step"] for r in recs[1:]] == [500, 1000, 1200]
+    assert [r["lattice_step"] for r in recs[1:]] == [500, 1000, 1200]
+    assert recs[-1]["S_w"] == hist[-1]["S_w"] and recs[-1]["mass2"] == 200.0
+    log2 = tmp_path / "pc.jsonl"
+    out = drivers.pc_sw_curve(lat, [0.0, 0.01], max_steps=3000, check_every=500, tol=0.06, log=log2)
+    recs = [json.loads(line) for line in log2.read_text().splitlines()]
+    assert len(recs) == 3 and [r["pc"] for r in recs[1:]] == [0.0, 0.01]
+    assert recs[1]["settled"] == out[0]["settled"]
+    # no path: nothing written, same results
+    assert drivers.drainage_history(_StandInLattice(solid), solid, 1200, every=500, outlet_slices=2) == hist

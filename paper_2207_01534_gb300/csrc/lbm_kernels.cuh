@@ -165,6 +165,15 @@ __device__ __forceinline__ float2 ld_pol(const float2 *q, unsigned long long pol
     return v;
 }
 __device__ __forceinline__ double2 ld_pol(const double2 *q, unsigned long long) { return __ldg(q); }
+// Stores of the density map under the same policy (the density and wall
+// passes write it; the wall and collide-stream passes read it back at once):
+// 128^3 pack FP32 0.0820 -> 0.0814 ms per step, FP16 unchanged.
+__device__ __forceinline__ void st_pol(float2 *q, float2 v, unsigned long long pol)
+{
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;" ::"l"(q), "f"(v.x), "f"(v.y), "l"(pol)
+                 : "memory");
+}
+__device__ __forceinline__ void st_pol(double2 *q, double2 v, unsigned long long) { *q = v; }
 // The same density-map loads for data written earlier in the same launch
 // (persistent kernels): ordinary coherent loads, which the compiler orders
 // against the launch's barriers like any other memory access.
@@ -656,7 +665,7 @@ __device__ __forceinline__ void dens_node_geo(int n, uint32_t pv, uint32_t fl, c
     const Nbr b = make_nbr(fl, s);
     C2 f[19], dm;
     load_pops<TS, P, LD_CA>(f, dm, n, pv, fl, b, s);
-    reinterpret_cast<C2 *>(s.psi)[pv] = density_of<TS>(dm, s);
+    st_pol(reinterpret_cast<C2 *>(s.psi) + pv, density_of<TS>(dm, s), l2_policy());
 }
 
 template <typename TS, int P>
@@ -713,7 +722,7 @@ __device__ __forceinline__ void wall_node_geo(int w, uint32_t pv, uint32_t mask,
         }
     }
     const C xi = reinterpret_cast<const C *>(s.wxi)[w];
-    psi[pv] = mul2(acc, mk2((C(1) + xi) * inv, (C(1) - xi) * inv));
+    st_pol(psi + pv, mul2(acc, mk2((C(1) + xi) * inv, (C(1) - xi) * inv)), l2_policy());
 }
 
 template <typename TS, int LD>

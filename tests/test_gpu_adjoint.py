@@ -143,6 +143,36 @@ def test_adjoint_against_finite_differences(lbm):
     assert abs(fd - grin) <= 1e-2 * abs(fd), (fd, grin)
 
 
+def test_dot_product_along_random_directions(lbm):
+    """<dJ/dxi, dxi> + dJ/drho_in1 drho against the change of J along a random
+    direction of every wall's xi and the inlet density together (FP64 storage,
+    central differences of the CUDA forward).  The perturbed xi fields are
+    rounded to float32 as the library stores them, so the directional change
+    is taken from the rounded fields themselves."""
+    case = _case(n=16, seed=8, nsteps=48)
+    solid, r1, r2, xi, kw, sample, nsteps = case
+    _, J0, gx, grin = _gpu_grad(lbm, "fp64", case, every=16)
+
+    def J_of(x, rin):
+        g = lbm.Lattice(solid, storage="fp64", kernel="split", sample=sample, **dict(kw, rho_in1=rin))
+        g.set_xi_field(x)
+        g.init_densities(r1, r2)
+        g.step(nsteps)
+        return g.saturation()[1]
+
+    rng = np.random.default_rng(31)
+    for trial in range(2):
+        dx = rng.standard_normal(solid.shape) * (solid == 1)
+        drho = float(rng.standard_normal())
+        eps = 1e-5
+        xp = (xi + eps * dx).astype(np.float32)
+        xm = (xi - eps * dx).astype(np.float32)
+        rp, rm = kw["rho_in1"] + eps * drho, kw["rho_in1"] - eps * drho
+        fd = J_of(xp, rp) - J_of(xm, rm)
+        ad = float((gx * (xp.astype(np.float64) - xm.astype(np.float64))).sum()) + grin * (rp - rm)
+        assert abs(fd - ad) <= 1e-4 * abs(fd), (trial, fd, ad)
+
+
 def test_reverse_pass_leaves_the_final_state(lbm):
     case = _case(nsteps=12)
     solid, r1, r2, xi, kw, sample, nsteps = case

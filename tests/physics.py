@@ -131,6 +131,28 @@ def duct_series_velocity(nxf, nyf, g, nu, nterms=101):
     return u
 
 
+def parallel_flow_profile(R, mu, g, fluid):
+    """Steady flow along x of a layered mixture between half-way walls:
+    d/dz (mu(z) du/dz) = -R(z) g on the fluid nodes of a column, u = 0 half
+    a node beyond the first and last fluid node.  Finite volumes with the
+    viscosity between two nodes taken as the harmonic mean of theirs (the
+    series resistance of two half cells).  R, mu and fluid are 1-D arrays over
+    z; returns u on the fluid nodes."""
+    idx = np.flatnonzero(fluid)
+    m = len(idx)
+    A = np.zeros((m, m))
+    for k in range(m):
+        i = idx[k]
+        for nb, kk in ((i - 1, k - 1), (i + 1, k + 1)):
+            if 0 <= kk < m:
+                mh = 2.0 * mu[i] * mu[nb] / (mu[i] + mu[nb])
+                A[k, k] -= mh
+                A[k, kk] += mh
+            else:
+                A[k, k] -= 2.0 * mu[i]  # wall half a node away
+    return np.linalg.solve(A, -np.asarray(R, float)[idx] * g)
+
+
 def trapped_by_dilation(rho1, rho2, solid, outlet_slices, periodic_xy=True):
     """Trapped wetting volume by repeated dilation (an algorithm independent
     of cluster labelling): start from the water voxels (rho2 > rho1, fluid) of

@@ -244,6 +244,29 @@ def test_enclosed_droplet_keeps_its_volume():
     assert abs(v1 - v0) <= 0.01 * v0, (v0, v1)
 
 
+def test_parallel_flow_solver_closed_forms():
+    """The momentum-balance solver the layered-flow pins use, against closed
+    forms: one viscosity gives the Poiseuille parabola with the walls half a
+    node beyond the fluid, and two layers with the jump on a cell face give
+    the two-layer solution (outer parabola, inner parabola plus the outer
+    layer's velocity at the interface), both to 0.2%."""
+    nz, g = 66, 1e-6
+    fluid = np.ones(nz, bool)
+    fluid[0] = fluid[-1] = False
+    y = np.arange(nz)[fluid] - (nz - 1) / 2.0
+    h, a = (nz - 2) / 2.0, 16.0
+    R = np.ones(nz)
+    u = physics.parallel_flow_profile(R, np.full(nz, 0.1), g, fluid)
+    ref = g / 0.2 * (h * h - y * y)
+    assert np.abs(u - ref).max() <= 2e-3 * ref.max()
+    mu_in, mu_out = 0.02, 0.2
+    mu = np.where(np.abs(np.arange(nz) - (nz - 1) / 2.0) < a, mu_in, mu_out)
+    u = physics.parallel_flow_profile(R, mu, g, fluid)
+    ref = np.where(np.abs(y) >= a, g / (2 * mu_out) * (h * h - y * y),
+                   g / (2 * mu_in) * (a * a - y * y) + g / (2 * mu_out) * (h * h - a * a))
+    assert np.abs(u - ref).max() <= 2e-3 * ref.max()
+
+
 @pytest.mark.parametrize("tau", [(1.0, 0.55), (0.5433, 0.9330)])
 def test_layered_channel_flow(tau):
     """Two immiscible layers driven along x between flat walls: component 1 in

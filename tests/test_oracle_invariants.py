@@ -111,6 +111,30 @@ def test_total_momentum_conserved_without_solids_equal_tau():
     assert np.abs(f["ux"]).max() > 1e-6
 
 
+@pytest.mark.parametrize("tau", [(1.0, 1.0), (1.7, 0.62)])
+def test_body_force_injects_exactly_its_momentum(tau):
+    """Periodic, solid-free, a droplet (so cohesion forces act) under a body
+    acceleration g: each step adds exactly F = sum_x R g to the total momentum,
+    whatever the relaxation times, because the velocity of the equilibrium
+    carries half the force (Eq. 8 with F/2) and the source term its factor
+    1 - 1/(2 tau) (Eq. 9): -(m - R u)/tau + (1 - 1/(2 tau)) F = F.  Without the
+    half-force shift at tau = 1 the collision keeps only F/2 per step."""
+    n, steps = 14, 100
+    solid = np.zeros((n, n, n), np.uint8)
+    r1, r2 = inputs.droplet_densities((n, n, n), (6.2, 7.7, 5.4), 4.0, 3.0, 1.0, 0.03)
+    g = np.array([2e-5, -1e-5, 3e-5])
+    o = oracle.Oracle(solid, tau=tau, G=3.5, body_force=tuple(g))
+    o.init_densities(r1, r2)
+    o.step(steps)
+    mass = sum(o.saturation()[2:])
+    assert np.abs(_momentum(o) / (steps * mass * g) - 1).max() < 1e-12
+    if tau == (1.0, 1.0):
+        q = oracle.Oracle(solid, tau=tau, G=3.5, body_force=tuple(g), velocity_shift=0)
+        q.init_densities(r1, r2)
+        q.step(steps)
+        assert np.abs(_momentum(q) / (steps * mass * g) - 0.5).max() < 1e-12
+
+
 def test_centred_droplet_keeps_cubic_symmetry():
     """A droplet centred on a node of a periodic cube keeps the 48 symmetries of
     the cube; any wrong component in the velocity table breaks it."""
